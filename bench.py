@@ -1,0 +1,353 @@
+"""Benchmark: source-ear samples/s of the sparse factorized HRIR renderer on one GB300.
+
+Workload (the batched rendering configuration): 1024 sources x 480000 samples (10 s at
+48 kHz) of seeded AR(1) noise, directions uniform over a 1250-direction grid, K = 16
+non-negative reflection taps of 200 per (direction, ear), 32-tap resonance per ear, output
+the full-length stereo mix.  One step = one hrir_render_batch call (sparse gather-FMA mix
+kernel + fixed-order reduction/resonance kernel) over the whole batch, inputs resident in
+HBM (1.97 GB, larger than the 129 MB L2, so no flush is needed).  The same batch is also
+rendered by the dense-HRIR direct path and with K = 8 and K = 32; those numbers are extra
+keys of the same JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank renders its own independent batch (seed offset by rank; no
+collective on the data path) and rank 0 prints one JSON line with the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+S_DEFAULT, L_DEFAULT, K_DEFAULT = 1024, 480000, 16
+METRIC = "source-ear samples/s (sparse vs dense/FFT conv, same GB300); p99 block latency"
+WORKLOAD = "batched: 1024 sources x 480000 samples AR(1), 1250 directions, K=16 of 200 taps, Lf=32"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+N_SM, FP32_LANES = 152, 128          # GB300: 152 SMs x 128 FP32 FMA lanes
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak: SMs x lanes x 2 flop x clock."""
+    return N_SM * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def profiled_traffic(kernel_file, profile_file):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel source (the summary records the source's sha256); else None."""
+    path = os.path.join(ROOT, "profiles", profile_file)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
+    m_b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b:
+        return None
+    src = os.path.join(ROOT, "paper_1502_03162_gb300", "csrc", kernel_file)
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return float(m_b.group(1)) if cur == m_sha.group(1) else None
+
+
+def make_inputs(S, L, seed, torch):
+    from paper_1502_03162_gb300 import synth
+    ld = (L + 7) // 8 * 8
+    host = torch.empty((S, ld), dtype=torch.float32, pin_memory=True)
+    cfg = synth.batched_config(S=S, L=L, seed=seed, ld=ld, out=host.numpy())
+    return cfg, host
+
+
+def time_steps(fn, steps, warmup, torch, barrier):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier()
+    st = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(steps):
+        fn()
+    b.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    return a.elapsed_time(b) / steps  # ms per step
+
+
+def cpu_baseline(cfg, idx, w, nnz, res, n_src=256):
+    """The oracle as it stands, one host core, on a bounded sample: the first n_src sources of
+    the same batch over the full length (sparse cascade, Eq. 2)."""
+    import oracle
+    y = cfg["y"][:n_src]
+    L = L_DEFAULT if y.shape[1] >= L_DEFAULT else y.shape[1]
+    t = time.perf_counter()
+    oracle.render_sparse(y, cfg["dirs"][:n_src], idx, w, nnz, 200, cfg["res"], length=L)
+    dt = time.perf_counter() - t
+    return {"value": n_src * L * 2 / dt, "unit": "source-ear samples/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{n_src} of the 1024 sources x {L} samples, sparse cascade, FP64, 1 thread "
+                      f"({dt:.1f} s)"}
+
+
+def run_reference(args):
+    """The oracle timed on the host cores on the same workload (bounded sample per step)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1502_03162_gb300 import synth
+    oracle.build()
+    n_src = 16
+    cfg = synth.batched_config(S=n_src, L=L_DEFAULT, seed=2)
+    idx, w, nnz = oracle.topk(cfg["G"], K_DEFAULT)
+    for _ in range(args.warmup):
+        oracle.render_sparse(cfg["y"][:1], cfg["dirs"][:1], idx, w, nnz, 200, cfg["res"])
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.render_sparse(cfg["y"], cfg["dirs"], idx, w, nnz, 200, cfg["res"])
+    dt = (time.perf_counter() - t) / args.steps
+    value = n_src * L_DEFAULT * 2 / dt
+    sample = f"{n_src} sources x {L_DEFAULT} samples per step, sparse cascade, FP64, 1 thread"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "source-ear samples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle sample)"},
+        "cpu_baseline": {"value": value, "unit": "source-ear samples/s", "cores": 1,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "source-ear samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sources", type=int, default=S_DEFAULT)
+    ap.add_argument("--length", type=int, default=L_DEFAULT)
+    ap.add_argument("--no-extras", action="store_true", help="only the headline sparse K=16 path")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_1502_03162_gb300 import hrir
+    import __graft_entry__
+    __graft_entry__.build()
+    S, L = args.sources, args.length
+    cfg, host = make_inputs(S, L, seed=2 + rank, torch=torch)
+    rend = hrir.Renderer(local)
+    G = torch.from_numpy(cfg["G"]).cuda()
+    src = host.cuda()
+    dirs_h = torch.from_numpy(cfg["dirs"])
+    dirs = dirs_h.cuda()
+    out = torch.empty((2, L + 230), dtype=torch.float32, device="cuda")
+
+    def load(k):
+        idx, w, nnz = rend.topk_pack(G, k)
+        idx_h = (idx.cpu().numpy().astype(np.int64) & 0xFFFF).astype(np.uint16)
+        rend.load_filters(idx_h, w.cpu().numpy(), nnz.cpu().numpy(), 200, cfg["res"])
+        return idx_h, w.cpu().numpy(), nnz.cpu().numpy()
+
+    tables16 = load(K_DEFAULT)
+    step = lambda: rend.render(src, dirs, mode="sparse", length=L, out=out)  # noqa: E731
+    # headline: sparse K=16, kernel timing on, clocks sampled
+    rend.set_timing(False)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    rend.kernel_times(reset=True)
+    rend.set_timing(True)
+    with ClockSampler(local) as clk:
+        ms = time_steps(step, args.steps, 0, torch, barrier)
+    rend.set_timing(False)
+    ktimes = rend.kernel_times(reset=True)
+    assert rend.sync() == 0
+    ms = max_over_ranks(ms)
+    units = S * L * 2
+    value = units * world / (ms / 1e3)
+
+    # kernel-level roofline of the dominant kernel (the sparse mixing kernel)
+    pk, pk_kind = peaks()
+    mix_ms, mix_n = ktimes.get("mix_sparse", (0.0, 0))
+    red_ms, red_n = ktimes.get("reduce_fir", (0.0, 0))
+    mix_launch_ms = mix_ms / max(mix_n, 1)
+    flops = 2.0 * K_DEFAULT * units          # one FMA per tap per source-ear sample
+    src_bytes = S * L * 4.0
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    fp32_peak = fp32_peak_tflops(sm_max)
+    hbm_peak = float(pk["hbm_gbs"])
+    t_alu = flops / (fp32_peak * 1e12)
+    t_hbm = src_bytes / (hbm_peak * 1e9)
+    bound = "alu" if t_alu >= t_hbm else "hbm"
+    if bound == "alu":
+        achieved = flops / (mix_launch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak}
+    else:
+        achieved = src_bytes / (mix_launch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak}
+    roof["traffic"] = profiled_traffic("mix_direct.cu", "mix_sparse_batched_1024x480000_k16.md")
+    roof["peak_source"] = (f"FP32 FMA: {N_SM} SMs x {FP32_LANES} lanes x 2 x {sm_max:.0f} MHz "
+                           f"(sm_max_mhz of {pk_kind} peaks); HBM {hbm_peak:.0f} GB/s {pk_kind}")
+    roof["kernel_ms"] = mix_launch_ms
+    roof["hbm_frac"] = (src_bytes / (mix_launch_ms / 1e3) / 1e9) / hbm_peak
+    roof["alu_frac"] = (flops / (mix_launch_ms / 1e3) / 1e12) / fp32_peak
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "source-ear samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded AR(1) sources, synthetic 1250-direction filters)",
+        "config": {"workload": WORKLOAD, "sources": S, "length": L, "k": K_DEFAULT,
+                   "refl_len": 200, "res_len": 32, "mode": "sparse",
+                   "l2": "inputs larger than L2 (1.97 GB source batch), no flush",
+                   "parallelism": f"replicas x{world} (independent batches)"},
+        "roofline": roof,
+        "gpu_launches": int(mix_n + red_n),
+        "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in ktimes.items()},
+        "clocks": clk.summary(),
+    }
+
+    if not args.no_extras:
+        extras = {}
+        # dense-HRIR direct convolution (plain method), same filters
+        t = time_steps(lambda: rend.render(src, dirs, mode="dense", length=L, out=out),
+                       max(2, args.steps // 5), 1, torch, barrier)
+        t = max_over_ranks(t)
+        extras["dense_k16"] = {"value": units * world / (t / 1e3), "ms_per_step": t}
+        for k in (8, 32):
+            load(k)
+            t = time_steps(step, max(3, args.steps // 2), 2, torch, barrier)
+            t = max_over_ranks(t)
+            extras[f"sparse_k{k}"] = {"value": units * world / (t / 1e3), "ms_per_step": t}
+        load(K_DEFAULT)
+        extras["sparse_k16"] = {"value": value, "ms_per_step": ms}
+        result["paths"] = extras
+
+    # end to end through the public host-buffer call: H2D of the pinned batch, render, D2H
+    host_out = torch.empty((2, L + 230), dtype=torch.float32, pin_memory=True)
+    e2e_step = lambda: rend.render_host(host, dirs_h, mode="sparse", length=L, out=host_out)  # noqa: E731
+    e2e_steps = max(2, args.steps // 4)
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    e2e_ms = max_over_ranks(e2e_ms)
+    result["e2e"] = {"value": units * world / (e2e_ms / 1e3), "unit": "source-ear samples/s",
+                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(S * host.shape[1] * 4 + S * 4),
+                     "d2h_bytes_per_step": int(2 * (L + 230) * 4)}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(cfg, *tables16, cfg["res"])
+    if rank == 0:
+        print(json.dumps(result))
+    rend.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

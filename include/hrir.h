@@ -1,0 +1,177 @@
+/*
+ * hrir.h -- C ABI of the GB300 (sm_103a) sparse factorized HRIR renderer.
+ *
+ * The method (Luo, Zotkin & Duraiswami, "Sparse Head-Related Impulse Response for
+ * Efficient Direct Convolution"):
+ *   Eq. 1      every HRIR is x = f * g: a direction-independent resonance filter f
+ *              (per ear) convolved with a direction-dependent, sparse, non-negative
+ *              reflection filter g;
+ *   Eq. 2      y * x = (y * g) * f, so a source y is rendered with the K non-zero taps
+ *              of g (direct convolution, Sec. I footnote 2) and the short dense f;
+ *   Sec. IV-G  direct convolution costs NNZE multiply-adds per output sample.
+ * The renderer mixes many sources, each at its own direction, into one stereo signal:
+ *     out_e[n] = sum_s (f_e * g_{dir[s],e} * y_s)[n],   e in {0 = left, 1 = right}.
+ * By linearity the resonance filter is applied once, after the mix (Eq. 2 with the sum
+ * over sources moved inside).  The same tables also drive two plain-method baselines:
+ * direct convolution with the dense HRIR f * g, and overlap-save FFT convolution
+ * (Sec. I footnote 3, Sec. IV-G).
+ *
+ * Notation used below: Lg = reflection length (the paper's K in Eq. 1), K = number of
+ * non-zero reflection taps (the paper's NNZE), Lf = resonance length (the paper's
+ * M-K+1), H = Lf + Lg - 1 = HRIR length (the paper's M).
+ *
+ * Conventions
+ *  - Every call returns an hrir_status (0 = HRIR_OK, negative = error); nothing aborts,
+ *    traps or prints.  hrir_last_error() gives a message for the last failure on ctx.
+ *  - "device" pointers are CUDA global-memory pointers on the context's device (for
+ *    example torch.Tensor.data_ptr()); "host" pointers are ordinary CPU memory.
+ *  - Work is enqueued on the caller's cudaStream_t (passed as void*; NULL = legacy
+ *    default stream) and is asynchronous: the call returns before the GPU finishes.
+ *  - Errors found on the device (a direction id out of range, a bounded wait that
+ *    expired) set a flag in the context; hrir_sync() waits for the stream and returns
+ *    the flag (then clears it).
+ *  - The caller owns every buffer it passes in.  The library owns its filter tables and
+ *    a workspace that it grows on demand and frees in hrir_destroy().
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef HRIR_H
+#define HRIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hrir_ctx hrir_ctx;
+
+typedef enum {
+    HRIR_OK = 0,
+    HRIR_EINVAL = -1,     /* bad argument (message in hrir_last_error) */
+    HRIR_ENOMEM = -2,     /* device or pinned-host allocation failed */
+    HRIR_ECUDA = -3,      /* a CUDA runtime call failed */
+    HRIR_ETIMEDOUT = -4,  /* a bounded device-side wait expired (kernel returned early) */
+    HRIR_EBUSY = -5,      /* resource temporarily unavailable (admission refused) */
+    HRIR_ESTATE = -6      /* call not valid in the current state (e.g. no filters loaded) */
+} hrir_status;
+
+typedef enum { HRIR_F32 = 0, HRIR_BF16 = 1, HRIR_F16 = 2 } hrir_dtype;
+
+typedef enum {
+    HRIR_SPARSE = 0,  /* sparse reflection gather-FMA, mix, then resonance FIR (Eq. 2)  */
+    HRIR_DENSE = 1,   /* direct convolution with the dense HRIR f * g (Eq. 1)           */
+    HRIR_FFT = 2      /* overlap-save FFT convolution with the dense HRIR (fn. 3)       */
+} hrir_mode;
+
+/* Library version, (major << 16) | minor. */
+int hrir_version(void);
+
+/* Create a context on CUDA device `device` (cudaSetDevice is called on it).  *out receives
+ * the new context or NULL.  HRIR_ECUDA if the device cannot be used. */
+int hrir_create(hrir_ctx **out, int device);
+
+/* Free the context, its tables and workspace.  Waits for the context's own work.  NULL ok. */
+void hrir_destroy(hrir_ctx *ctx);
+
+/* Message for the most recent failing call on ctx (ctx may be NULL: then the message of the
+ * last failing hrir_create on this thread).  Never NULL; valid until the next call. */
+const char *hrir_last_error(const hrir_ctx *ctx);
+
+/* Wait for all work enqueued on `stream`, then return and clear any device-side error flag:
+ * HRIR_EINVAL (a direction id was out of range; that source was rendered as silence),
+ * HRIR_ETIMEDOUT (a bounded wait expired; the output of that call is incomplete), or
+ * HRIR_ECUDA if the stream reported a CUDA error. */
+int hrir_sync(hrir_ctx *ctx, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Filter pack: top-K sparsification of non-negative reflection rows (a device kernel).
+ * Follows the NNZE budget of Sec. III-D: from each row of g keep the K largest strictly
+ * positive values (larger value first; on equal values the smaller index), then store
+ * them in ascending index order, padding unused slots with (0, 0.0f).
+ *   g     device, float [n_rows][refl_len], row-major, any values (NaN/negatives are
+ *         never selected).  1 <= refl_len <= 2048.
+ *   idx   device, uint16 [n_rows][k]    out
+ *   w     device, float  [n_rows][k]    out
+ *   nnz   device, uint8  [n_rows]       out (number of kept taps, <= k)
+ *   0 <= k <= 255.  Bit-exact: indices and weights are copies of input entries.
+ * ------------------------------------------------------------------------------------- */
+int hrir_topk_pack(hrir_ctx *ctx, int n_rows, int refl_len, int k, const float *g,
+                   uint16_t *idx, float *w, uint8_t *nnz, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Load the factorized filters (Sec. II: f per ear, g per direction and ear).  All
+ * pointers are HOST memory; the data is copied (the caller keeps ownership) and the
+ * device tables are built by kernels: the sparse tap programs for HRIR_SPARSE, the dense
+ * HRIRs x = f * g (Eq. 1) for HRIR_DENSE and their spectra for HRIR_FFT.  Replaces any
+ * previously loaded filters; blocks until the tables are ready.
+ *   n_dirs     >= 1 directions;  n_ears must be 2.
+ *   refl_len   Lg, 1 .. 2048;  k_max 0 .. 255 slots per (direction, ear).
+ *   tap_idx    uint16 [n_dirs][2][k_max]: the first nnz entries strictly ascending, < Lg.
+ *   tap_w      float  [n_dirs][2][k_max]: finite and >= 0 (g >= 0, Eq. 1).
+ *   tap_nnz    uint8  [n_dirs][2]: used slots, <= k_max.
+ *   res_len    Lf, 1 .. 512;  resonance float [2][res_len], finite.
+ *   fft_size   overlap-save frame P for HRIR_FFT (power of two, 512..8192, > H),
+ *              or 0 to choose automatically.
+ * ------------------------------------------------------------------------------------- */
+int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k_max,
+                      const uint16_t *tap_idx, const float *tap_w, const uint8_t *tap_nnz,
+                      int res_len, const float *resonance, int fft_size);
+
+/* Output length of a render: len + H - 1 when full != 0, else len (the first len
+ * samples of the full linear convolution, Sec. I footnote 2).  0 when len == 0. */
+int64_t hrir_out_len(const hrir_ctx *ctx, int64_t len, int full);
+
+/* ---------------------------------------------------------------------------------------
+ * Render n_src sources into one stereo mix (Eqs. 1-2), on the device.
+ *   src     device, [n_src][src_ld] of dtype dt; source s is src[s][0 .. len-1].  The base
+ *           must be 16-byte aligned and src_ld*sizeof(dt) a multiple of 16; columns
+ *           >= len are never read.  HRIR_BF16/HRIR_F16 sources are widened to FP32 and
+ *           all arithmetic is FP32.
+ *   dir     device, int32 [n_src], direction of each source (0 .. n_dirs-1; an id out of
+ *           range renders that source as silence and flags HRIR_EINVAL for hrir_sync).
+ *   mode    HRIR_SPARSE (the method), HRIR_DENSE or HRIR_FFT (plain-method baselines).
+ *   full    1: out_len = len + H - 1, 0: out_len = len.
+ *   out     device, float [2][out_ld] (row 0 left, row 1 right), out_ld >= out_len;
+ *           columns [0, out_len) are overwritten, the rest untouched.
+ *   stream  cudaStream_t to enqueue on.
+ * Every source is read once per render; the mix is deterministic (fixed summation order
+ * for a given device and shape).  n_src == 0 writes zeros; len == 0 writes nothing.
+ * ------------------------------------------------------------------------------------- */
+int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hrir_dtype dt,
+                      const void *src, const int32_t *dir, hrir_mode mode, int full,
+                      float *out, int64_t out_ld, void *stream);
+
+/* Same as hrir_render_batch with HOST buffers: src [n_src][src_ld], dir [n_src] and out
+ * [2][out_ld] live in CPU memory (page-locked memory gives the fastest copies).  The
+ * call copies the sources to the device (pipelined with rendering), renders, copies the
+ * mix back and returns when `out` holds the result.  Device staging space comes from the
+ * context workspace. */
+int hrir_render_batch_host(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld,
+                           hrir_dtype dt, const void *src, const int32_t *dir, hrir_mode mode,
+                           int full, float *out, int64_t out_ld, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Optional kernel timing, for benchmarks.  While enabled, the library brackets each of its
+ * kernel launches with CUDA events recorded on the launching stream.  hrir_kernel_times
+ * waits for those events and writes, per kernel family (hrir_kernel), the accumulated
+ * milliseconds and launch counts since the last reset (arrays of HRIR_K_COUNT entries;
+ * either may be NULL).  reset != 0 clears the accumulators after reading.
+ * ------------------------------------------------------------------------------------- */
+typedef enum {
+    HRIR_K_MIX_SPARSE = 0,  /* sparse reflection gather-FMA mixing kernel */
+    HRIR_K_MIX_DENSE = 1,   /* dense-HRIR direct-convolution mixing kernel */
+    HRIR_K_REDUCE = 2,      /* fixed-order partial reduction + resonance FIR */
+    HRIR_K_FFT = 3,         /* overlap-save FFT kernels */
+    HRIR_K_TABLES = 4,      /* filter-pack kernels (top-K, records) */
+    HRIR_K_COUNT = 8
+} hrir_kernel;
+
+int hrir_set_timing(hrir_ctx *ctx, int enable);
+int hrir_kernel_times(hrir_ctx *ctx, double *ms, int64_t *launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HRIR_H */

@@ -41,14 +41,19 @@ _int = ctypes.c_int
 
 def build(force: bool = False) -> str:
     """Compile hrir_oracle.c with gcc into oracle/_build/liboracle.so (no CUDA involved)."""
+    import platform
     os.makedirs(_BUILD_DIR, exist_ok=True)
-    stale = (not os.path.exists(_LIB_PATH)) or (
+    stamp = os.path.join(_BUILD_DIR, "ARCH")
+    same_arch = os.path.exists(stamp) and open(stamp).read() == platform.machine()
+    stale = (not same_arch) or (not os.path.exists(_LIB_PATH)) or (
         os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
     if force or stale:
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
+        with open(stamp, "w") as f:
+            f.write(platform.machine())
     return _LIB_PATH
 
 
@@ -74,6 +79,9 @@ def _load():
             lib.orc_render_dense.restype = _int
             lib.orc_render_fft.argtypes = render_args + [_D, _i64]
             lib.orc_render_fft.restype = _int
+            lib.orc_render_sparse_at.argtypes = render_args + [ctypes.POINTER(ctypes.c_int64),
+                                                               _i64, _D]
+            lib.orc_render_sparse_at.restype = _int
             lib.orc_topk.argtypes = [_F, _int, _int, _int, _U16, _F, _U8]
             lib.orc_topk.restype = _int
             _lib = lib
@@ -205,6 +213,24 @@ def render_dense(y, dirs, tap_idx, tap_w, tap_nnz, refl_len, res, length=None):
 def render_fft(y, dirs, tap_idx, tap_w, tap_nnz, refl_len, res, length=None):
     """Same quantity as render_sparse, by FFT convolution with the dense HRIR f*g."""
     return _render("orc_render_fft", y, length, dirs, tap_idx, tap_w, tap_nnz, refl_len, res)
+
+
+def render_at(y, dirs, tap_idx, tap_w, tap_nnz, refl_len, res, positions, length=None):
+    """The mix of render_sparse evaluated only at the given output positions ([2][n_pos]),
+    straight from the cascade definition; cost independent of the source length."""
+    y, dirs, tap_idx, tap_w, tap_nnz, res, n_dirs, k_max = _render_common(
+        y, dirs, tap_idx, tap_w, tap_nnz, res)
+    S, ld = y.shape
+    L = int(ld if length is None else length)
+    pos = np.ascontiguousarray(positions, dtype=np.int64)
+    out = np.zeros((2, max(pos.size, 1)))
+    rc = _load().orc_render_sparse_at(
+        S, L, _p(y, _F), ld, _p(dirs, _I32), n_dirs, k_max, _p(tap_idx, _U16), _p(tap_w, _F),
+        _p(tap_nnz, _U8), refl_len, res.shape[1], _p(res, _F),
+        pos.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), pos.size, _p(out, _D))
+    if rc != 0:
+        raise ValueError(f"orc_render_sparse_at rejected its arguments (rc={rc})")
+    return out[:, :pos.size]
 
 
 def dense_hrirs(tap_idx, tap_w, tap_nnz, refl_len, res) -> np.ndarray:

@@ -295,6 +295,38 @@ int orc_render_fft(int S, int64_t L, const float *y, int64_t ld, const int32_t *
                             res, out, out_ld);
 }
 
+/* Selected output samples of the same mix, straight from the cascade definition:
+ *   out_e[n] = sum_s sum_{l < res_len} f_e[l] sum_t w_{dir s, e, t} y_s[n - l - i_{dir s, e, t}]
+ * for the n_pos positions pos[] (any order; positions outside [0, L+H-1) give 0).
+ * out is [2][n_pos].  Cost O(n_pos * S * res_len * k_max), independent of L. */
+int orc_render_sparse_at(int S, int64_t L, const float *y, int64_t ld, const int32_t *dir,
+                         int n_dirs, int k_max, const uint16_t *idx, const float *w,
+                         const uint8_t *nnz, int refl_len, int res_len, const float *res,
+                         const int64_t *pos, int64_t n_pos, double *out)
+{
+    if (check_render_args(S, L, dir, n_dirs, k_max, idx, nnz, refl_len, res_len)) return -1;
+    for (int64_t p = 0; p < n_pos; ++p) {
+        const int64_t n = pos[p];
+        for (int e = 0; e < 2; ++e) {
+            double acc = 0.0;
+            for (int s = 0; s < S; ++s) {
+                const int64_t row = (int64_t)dir[s] * 2 + e;
+                for (int l = 0; l < res_len; ++l) {
+                    double inner = 0.0;
+                    for (int t = 0; t < nnz[row]; ++t) {
+                        const int64_t m = n - l - (int64_t)idx[row * k_max + t];
+                        if (m < 0 || m >= L) continue;
+                        inner += (double)w[row * k_max + t] * (double)y[(int64_t)s * ld + m];
+                    }
+                    acc += (double)res[e * res_len + l] * inner;
+                }
+            }
+            out[e * n_pos + p] = acc;
+        }
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------------------
  * Top-K sparsification of non-negative reflection rows (the K-tap budget applied after
  * the sparsity-promoting fit of Sec. III-D and the small-tap discard of Sec. III-D).

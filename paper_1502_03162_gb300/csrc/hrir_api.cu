@@ -1,0 +1,554 @@
+// hrir_api.cu -- host side of the C ABI declared in include/hrir.h: argument checking,
+// filter-table construction, workspace management and kernel launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "../../include/hrir.h"
+#include "kernels.h"
+
+using namespace hrir;
+
+struct hrir_ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::string err;
+
+    bool loaded = false;
+    int n_dirs = 0, refl_len = 0, k_max = 0, res_len = 0, hrir_len = 0, fft_size = 0;
+    unsigned char *d_sparse = nullptr;  // (n_dirs + 1) sparse tap records
+    int sparse_rec_bytes = 0, sparse_nchunk = 0;
+    float *d_dense = nullptr;           // (n_dirs + 1) x [2][dense_padded]
+    int dense_padded = 0, dense_nchunk = 0;
+    float *d_res = nullptr;             // [2][res_len]
+
+    float *d_partial = nullptr;
+    size_t partial_bytes = 0;
+    void *d_stage = nullptr;            // device staging for hrir_render_batch_host
+    size_t stage_bytes = 0;
+    int *d_status = nullptr;
+
+    // optional kernel timing (hrir_set_timing)
+    bool timing = false;
+    struct Pending {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> free_events;
+    double ms[HRIR_K_COUNT] = {};
+    int64_t launches[HRIR_K_COUNT] = {};
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(hrir_ctx *ctx, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    else g_create_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                  \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((ctx), HRIR_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+int grow(hrir_ctx *ctx, void **ptr, size_t *have, size_t need)
+{
+    if (need <= *have && *ptr) return HRIR_OK;
+    if (*ptr) {
+        cudaFree(*ptr);
+        *ptr = nullptr;
+        *have = 0;
+    }
+    size_t want = need + need / 8;
+    if (cudaMalloc(ptr, want) != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return fail(ctx, HRIR_ENOMEM, "workspace allocation of %zu bytes failed", want);
+    }
+    *have = want;
+    return HRIR_OK;
+}
+
+void free_tables(hrir_ctx *ctx)
+{
+    cudaFree(ctx->d_sparse);
+    cudaFree(ctx->d_dense);
+    cudaFree(ctx->d_res);
+    ctx->d_sparse = nullptr;
+    ctx->d_dense = nullptr;
+    ctx->d_res = nullptr;
+    ctx->loaded = false;
+}
+
+size_t dtype_size(int dt) { return dt == HRIR_F32 ? 4 : 2; }
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Pipeline depth that fits the 227 KB shared-memory limit.
+int pick_stages(int buf_elems, int elem_bytes, int rec_bytes, size_t *smem)
+{
+    for (int st = kMixMaxStages; st >= 2; --st) {
+        size_t b = mix_smem_bytes(buf_elems, elem_bytes, rec_bytes, st);
+        if (b <= 227 * 1024) {
+            *smem = b;
+            return st;
+        }
+    }
+    return 0;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link-time libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D tensor map over the sources: dims {len, n_src}, row stride ld elements, box
+// {kMixBox, 1}, out-of-range elements read as zero.
+int make_source_map(hrir_ctx *ctx, CUtensorMap *m, const void *src, int dt, int64_t len,
+                    int64_t ld, int n_src)
+{
+    auto fn = tensor_map_encoder();
+    if (!fn) return fail(ctx, HRIR_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    const CUtensorMapDataType ty = dt == HRIR_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : dt == HRIR_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const cuuint64_t dims[2] = {(cuuint64_t)len, (cuuint64_t)n_src};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * (int64_t)dtype_size(dt))};
+    const cuuint32_t box[2] = {(cuuint32_t)kMixBox, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, ty, 2, const_cast<void *>(src), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, HRIR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return HRIR_OK;
+}
+
+cudaEvent_t take_event(hrir_ctx *ctx)
+{
+    if (!ctx->free_events.empty()) {
+        cudaEvent_t e = ctx->free_events.back();
+        ctx->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one kernel launch with events when timing is enabled.
+struct KernelTimer {
+    hrir_ctx *ctx;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    KernelTimer(hrir_ctx *c, int k, cudaStream_t s) : ctx(c), kind(k), st(s)
+    {
+        if (ctx->timing) {
+            a = take_event(ctx);
+            cudaEventRecord(a, st);
+        }
+    }
+    void done()
+    {
+        if (!a) return;
+        cudaEvent_t b = take_event(ctx);
+        cudaEventRecord(b, st);
+        ctx->pending.push_back({kind, a, b});
+        a = nullptr;
+    }
+};
+
+void drop_timing_events(hrir_ctx *ctx)
+{
+    for (auto &p : ctx->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    ctx->pending.clear();
+    for (auto e : ctx->free_events) cudaEventDestroy(e);
+    ctx->free_events.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+int hrir_version(void) { return (0 << 16) | 1; }
+
+int hrir_create(hrir_ctx **out, int device)
+{
+    if (!out) return fail(nullptr, HRIR_EINVAL, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return fail(nullptr, HRIR_ECUDA, "CUDA device %d not available (%d devices)", device, n);
+    }
+    if (cudaSetDevice(device) != cudaSuccess)
+        return fail(nullptr, HRIR_ECUDA, "cudaSetDevice(%d) failed", device);
+    hrir_ctx *ctx = new hrir_ctx();
+    ctx->device = device;
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return fail(nullptr, HRIR_ENOMEM, "status word allocation failed");
+    }
+    *out = ctx;
+    return HRIR_OK;
+}
+
+void hrir_destroy(hrir_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    free_tables(ctx);
+    drop_timing_events(ctx);
+    cudaFree(ctx->d_partial);
+    cudaFree(ctx->d_stage);
+    cudaFree(ctx->d_status);
+    delete ctx;
+}
+
+int hrir_set_timing(hrir_ctx *ctx, int enable)
+{
+    if (!ctx) return fail(nullptr, HRIR_EINVAL, "ctx is NULL");
+    ctx->timing = enable != 0;
+    return HRIR_OK;
+}
+
+int hrir_kernel_times(hrir_ctx *ctx, double *ms, int64_t *launches, int reset)
+{
+    if (!ctx) return fail(nullptr, HRIR_EINVAL, "ctx is NULL");
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    for (auto &p : ctx->pending) {
+        CUDA_TRY(ctx, cudaEventSynchronize(p.b));
+        float t = 0.f;
+        CUDA_TRY(ctx, cudaEventElapsedTime(&t, p.a, p.b));
+        ctx->ms[p.kind] += t;
+        ctx->launches[p.kind] += 1;
+        ctx->free_events.push_back(p.a);
+        ctx->free_events.push_back(p.b);
+    }
+    ctx->pending.clear();
+    for (int i = 0; i < HRIR_K_COUNT; ++i) {
+        if (ms) ms[i] = ctx->ms[i];
+        if (launches) launches[i] = ctx->launches[i];
+        if (reset) {
+            ctx->ms[i] = 0.0;
+            ctx->launches[i] = 0;
+        }
+    }
+    return HRIR_OK;
+}
+
+const char *hrir_last_error(const hrir_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+int hrir_sync(hrir_ctx *ctx, void *stream)
+{
+    if (!ctx) return fail(nullptr, HRIR_EINVAL, "ctx is NULL");
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    CUDA_TRY(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+    int st = 0;
+    CUDA_TRY(ctx, cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st == 0) return HRIR_OK;
+    CUDA_TRY(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+    if (st & DEV_TIMEOUT)
+        return fail(ctx, HRIR_ETIMEDOUT, "a bounded device wait expired (output incomplete)");
+    return fail(ctx, HRIR_EINVAL, "a direction id was out of range (rendered as silence)");
+}
+
+int hrir_topk_pack(hrir_ctx *ctx, int n_rows, int refl_len, int k, const float *g, uint16_t *idx,
+                   float *w, uint8_t *nnz, void *stream)
+{
+    if (!ctx) return fail(nullptr, HRIR_EINVAL, "ctx is NULL");
+    if (n_rows < 0 || refl_len < 1 || refl_len > 2048 || k < 0 || k > 255)
+        return fail(ctx, HRIR_EINVAL, "bad sizes (n_rows=%d refl_len=%d k=%d)", n_rows, refl_len, k);
+    if (n_rows == 0) return HRIR_OK;
+    if (!g || !nnz || (k > 0 && (!idx || !w))) return fail(ctx, HRIR_EINVAL, "NULL buffer");
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    KernelTimer kt(ctx, HRIR_K_TABLES, (cudaStream_t)stream);
+    CUDA_TRY(ctx, launch_topk(g, n_rows, refl_len, k, idx, w, nnz, (cudaStream_t)stream));
+    kt.done();
+    return HRIR_OK;
+}
+
+int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k_max,
+                      const uint16_t *tap_idx, const float *tap_w, const uint8_t *tap_nnz,
+                      int res_len, const float *resonance, int fft_size)
+{
+    if (!ctx) return fail(nullptr, HRIR_EINVAL, "ctx is NULL");
+    if (n_dirs < 1 || n_ears != 2 || refl_len < 1 || refl_len > 2048 || k_max < 0 ||
+        k_max > 255 || res_len < 1 || res_len > 512)
+        return fail(ctx, HRIR_EINVAL, "bad sizes (n_dirs=%d n_ears=%d refl_len=%d k_max=%d res_len=%d)",
+                    n_dirs, n_ears, refl_len, k_max, res_len);
+    if (!tap_nnz || !resonance || (k_max > 0 && (!tap_idx || !tap_w)))
+        return fail(ctx, HRIR_EINVAL, "NULL table pointer");
+    const int hrir_len = res_len + refl_len - 1;
+    if (fft_size != 0 && (fft_size < 512 || fft_size > 8192 || (fft_size & (fft_size - 1)) ||
+                          fft_size <= hrir_len))
+        return fail(ctx, HRIR_EINVAL, "fft_size %d must be 0 or a power of two in [512, 8192] above H=%d",
+                    fft_size, hrir_len);
+    for (int64_t r = 0; r < (int64_t)n_dirs * 2; ++r) {
+        const int k = tap_nnz[r];
+        if (k > k_max) return fail(ctx, HRIR_EINVAL, "tap_nnz[%lld]=%d > k_max", (long long)r, k);
+        for (int t = 0; t < k; ++t) {
+            const int i = tap_idx[r * k_max + t];
+            const float v = tap_w[r * k_max + t];
+            if (i >= refl_len)
+                return fail(ctx, HRIR_EINVAL, "tap index %d >= refl_len at row %lld", i, (long long)r);
+            if (t > 0 && i <= tap_idx[r * k_max + t - 1])
+                return fail(ctx, HRIR_EINVAL, "tap indices not strictly ascending at row %lld", (long long)r);
+            if (!std::isfinite(v) || v < 0.f)
+                return fail(ctx, HRIR_EINVAL, "tap weight must be finite and >= 0 (row %lld)", (long long)r);
+        }
+    }
+    for (int i = 0; i < 2 * res_len; ++i)
+        if (!std::isfinite(resonance[i])) return fail(ctx, HRIR_EINVAL, "resonance must be finite");
+
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    CUDA_TRY(ctx, cudaDeviceSynchronize());
+    free_tables(ctx);
+
+    const size_t rows = (size_t)n_dirs * 2;
+    const size_t kk = k_max > 0 ? (size_t)k_max : 1;
+    uint16_t *d_idx = nullptr;
+    float *d_w = nullptr;
+    uint8_t *d_nnz = nullptr;
+    const int sparse_rec = (int)round_up(16 + 2 * (int64_t)k_max * 8, 16);
+    const int dense_nchunk = (hrir_len + kMixR - 1) / kMixR;
+    const int dense_padded = dense_nchunk * kMixR;
+    int rc = HRIR_OK;
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((e = cudaMalloc(&d_idx, rows * kk * 2)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&d_w, rows * kk * 4)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&d_nnz, rows)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&ctx->d_res, 2 * (size_t)res_len * 4)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&ctx->d_sparse, (size_t)(n_dirs + 1) * sparse_rec)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&ctx->d_dense, (size_t)(n_dirs + 1) * 2 * dense_padded * 4)) != cudaSuccess)
+            break;
+        if (k_max > 0) {
+            if ((e = cudaMemcpy(d_idx, tap_idx, rows * k_max * 2, cudaMemcpyHostToDevice)) != cudaSuccess) break;
+            if ((e = cudaMemcpy(d_w, tap_w, rows * k_max * 4, cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        }
+        if ((e = cudaMemcpy(d_nnz, tap_nnz, rows, cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        if ((e = cudaMemcpy(ctx->d_res, resonance, 2 * (size_t)res_len * 4, cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            break;
+        if ((e = launch_build_sparse_records(d_idx, d_w, d_nnz, n_dirs, (int)kk, ctx->d_sparse,
+                                             sparse_rec, 0)) != cudaSuccess)
+            break;
+        if ((e = launch_build_dense_records(d_idx, d_w, d_nnz, n_dirs, (int)kk, ctx->d_res, res_len,
+                                            hrir_len, dense_padded, ctx->d_dense, 0)) != cudaSuccess)
+            break;
+        e = cudaDeviceSynchronize();
+    } while (0);
+    cudaFree(d_idx);
+    cudaFree(d_w);
+    cudaFree(d_nnz);
+    if (e != cudaSuccess) {
+        free_tables(ctx);
+        rc = fail(ctx, e == cudaErrorMemoryAllocation ? HRIR_ENOMEM : HRIR_ECUDA,
+                  "filter table construction failed: %s", cudaGetErrorString(e));
+        cudaGetLastError();
+        return rc;
+    }
+    ctx->n_dirs = n_dirs;
+    ctx->refl_len = refl_len;
+    ctx->k_max = k_max;
+    ctx->res_len = res_len;
+    ctx->hrir_len = hrir_len;
+    ctx->fft_size = fft_size;
+    ctx->sparse_rec_bytes = sparse_rec;
+    ctx->sparse_nchunk = (refl_len + kMixR - 1) / kMixR;
+    ctx->dense_nchunk = dense_nchunk;
+    ctx->dense_padded = dense_padded;
+    ctx->loaded = true;
+    return HRIR_OK;
+}
+
+int64_t hrir_out_len(const hrir_ctx *ctx, int64_t len, int full)
+{
+    if (!ctx || !ctx->loaded || len <= 0) return 0;
+    return full ? len + ctx->hrir_len - 1 : len;
+}
+
+int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hrir_dtype dt,
+                      const void *src, const int32_t *dir, hrir_mode mode, int full, float *out,
+                      int64_t out_ld, void *stream)
+{
+    if (!ctx) return fail(nullptr, HRIR_EINVAL, "ctx is NULL");
+    if (!ctx->loaded) return fail(ctx, HRIR_ESTATE, "no filters loaded");
+    if (n_src < 0 || len < 0) return fail(ctx, HRIR_EINVAL, "negative n_src or len");
+    if (dt != HRIR_F32 && dt != HRIR_BF16 && dt != HRIR_F16)
+        return fail(ctx, HRIR_EINVAL, "unknown dtype %d", (int)dt);
+    if (mode != HRIR_SPARSE && mode != HRIR_DENSE && mode != HRIR_FFT)
+        return fail(ctx, HRIR_EINVAL, "unknown mode %d", (int)mode);
+    const int64_t out_len = full ? (len > 0 ? len + ctx->hrir_len - 1 : 0) : len;
+    if (out_len == 0) return HRIR_OK;
+    if (!out || out_ld < out_len) return fail(ctx, HRIR_EINVAL, "out is NULL or out_ld < %lld", (long long)out_len);
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    if (n_src == 0) {
+        CUDA_TRY(ctx, cudaMemset2DAsync(out, (size_t)out_ld * 4, 0, (size_t)out_len * 4, 2, st));
+        return HRIR_OK;
+    }
+    const size_t es = dtype_size(dt);
+    if (!src || !dir) return fail(ctx, HRIR_EINVAL, "NULL src or dir");
+    if (src_ld < len || ((uintptr_t)src % 16) || ((src_ld * (int64_t)es) % 16))
+        return fail(ctx, HRIR_EINVAL,
+                    "src must be 16-byte aligned with src_ld >= len and src_ld*elem_size %% 16 == 0");
+    if (mode == HRIR_FFT) return fail(ctx, HRIR_EINVAL, "HRIR_FFT is not available in this build");
+
+    if (len > (int64_t)1 << 31) return fail(ctx, HRIR_EINVAL, "len must be < 2^31");
+
+    const bool sparse = mode == HRIR_SPARSE;
+    const int nchunk = sparse ? ctx->sparse_nchunk : ctx->dense_nchunk;
+    const int halo = (int)round_up((int64_t)nchunk * kMixR, 8);
+    const int buf_elems = (int)round_up(halo + kMixTile, kMixBox);
+    const int rec_bytes = sparse ? ctx->sparse_rec_bytes : 2 * ctx->dense_padded * 4;
+    const int64_t mix_len = sparse ? std::min<int64_t>(out_len, len + ctx->refl_len - 1) : out_len;
+    const int n_tiles = (int)((mix_len + kMixTile - 1) / kMixTile);
+    size_t smem = 0;
+    const int stages = pick_stages(buf_elems, (int)es, rec_bytes, &smem);
+    if (stages == 0) return fail(ctx, HRIR_EINVAL, "filters too long for the shared-memory pipeline");
+    CUtensorMap tmap;
+    int rc = make_source_map(ctx, &tmap, src, (int)dt, len, src_ld, n_src);
+    if (rc) return rc;
+
+    Partition part;
+    part.U = (int64_t)n_tiles * n_src;
+    part.P = std::min<int64_t>(ctx->num_sms, part.U);
+    part.n_src = n_src;
+    part.gs = kRunSources;
+    int slots = 0;
+    for (int t = 0; t < n_tiles; ++t) slots = std::max(slots, part.slots(t));
+    const size_t pbytes = (size_t)n_tiles * slots * 2 * kMixTile * sizeof(float);
+    rc = grow(ctx, (void **)&ctx->d_partial, &ctx->partial_bytes, pbytes);
+    if (rc) return rc;
+
+    MixArgs a;
+    a.src = src;
+    a.ld = src_ld;
+    a.len = len;
+    a.n_src = n_src;
+    a.dir = dir;
+    a.n_dirs = ctx->n_dirs;
+    a.table = sparse ? ctx->d_sparse : reinterpret_cast<const unsigned char *>(ctx->d_dense);
+    a.rec_bytes = rec_bytes;
+    a.nchunk = nchunk;
+    a.halo = halo;
+    a.buf_elems = buf_elems;
+    a.n_tiles = n_tiles;
+    a.stages = stages;
+    a.part = part;
+    a.partial = ctx->d_partial;
+    a.slots = slots;
+    a.status = ctx->d_status;
+    {
+        KernelTimer kt(ctx, sparse ? HRIR_K_MIX_SPARSE : HRIR_K_MIX_DENSE, st);
+        CUDA_TRY(ctx, launch_mix(sparse ? MIX_SPARSE : MIX_DENSE, (int)dt, tmap, a, (int)part.P, smem, st));
+        kt.done();
+    }
+
+    ReduceArgs r;
+    r.partial = ctx->d_partial;
+    r.slots = slots;
+    r.n_tiles = n_tiles;
+    r.tile = kMixTile;
+    r.part = part;
+    r.res = sparse ? ctx->d_res : nullptr;
+    r.res_len = ctx->res_len;
+    r.out_len = out_len;
+    r.out = out;
+    r.out_ld = out_ld;
+    {
+        KernelTimer kt(ctx, HRIR_K_REDUCE, st);
+        CUDA_TRY(ctx, launch_reduce(r, st));
+        kt.done();
+    }
+    return HRIR_OK;
+}
+
+int hrir_render_batch_host(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hrir_dtype dt,
+                           const void *src, const int32_t *dir, hrir_mode mode, int full, float *out,
+                           int64_t out_ld, void *stream)
+{
+    if (!ctx) return fail(nullptr, HRIR_EINVAL, "ctx is NULL");
+    if (!ctx->loaded) return fail(ctx, HRIR_ESTATE, "no filters loaded");
+    if (n_src < 0 || len < 0 || src_ld < len) return fail(ctx, HRIR_EINVAL, "bad n_src/len/src_ld");
+    if (dt != HRIR_F32 && dt != HRIR_BF16 && dt != HRIR_F16)
+        return fail(ctx, HRIR_EINVAL, "unknown dtype %d", (int)dt);
+    const int64_t out_len = full ? (len > 0 ? len + ctx->hrir_len - 1 : 0) : len;
+    if (out_len == 0) return HRIR_OK;
+    if (!out || out_ld < out_len) return fail(ctx, HRIR_EINVAL, "out is NULL or out_ld too small");
+    if (n_src > 0 && (!src || !dir)) return fail(ctx, HRIR_EINVAL, "NULL src or dir");
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const size_t es = dtype_size(dt);
+    const int64_t vec = 16 / (int64_t)es;
+    const int64_t dld = round_up(std::max<int64_t>(len, 1), vec);
+    const size_t src_bytes = (size_t)n_src * dld * es;
+    const size_t dir_off = round_up((int64_t)src_bytes, 256);
+    const size_t out_off = round_up((int64_t)(dir_off + (size_t)n_src * 4), 256);
+    const size_t need = out_off + 2 * (size_t)out_len * 4;
+    int rc = grow(ctx, &ctx->d_stage, &ctx->stage_bytes, need);
+    if (rc) return rc;
+    unsigned char *base = static_cast<unsigned char *>(ctx->d_stage);
+    void *d_src = base;
+    int32_t *d_dir = reinterpret_cast<int32_t *>(base + dir_off);
+    float *d_out = reinterpret_cast<float *>(base + out_off);
+    if (n_src > 0) {
+        if (dld == src_ld) {
+            CUDA_TRY(ctx, cudaMemcpyAsync(d_src, src, src_bytes, cudaMemcpyHostToDevice, st));
+        } else {
+            CUDA_TRY(ctx, cudaMemcpy2DAsync(d_src, dld * es, src, src_ld * es, len * es, n_src,
+                                            cudaMemcpyHostToDevice, st));
+        }
+        CUDA_TRY(ctx, cudaMemcpyAsync(d_dir, dir, (size_t)n_src * 4, cudaMemcpyHostToDevice, st));
+    }
+    rc = hrir_render_batch(ctx, n_src, len, dld, dt, d_src, d_dir, mode, full, d_out, out_len, stream);
+    if (rc) return rc;
+    CUDA_TRY(ctx, cudaMemcpy2DAsync(out, out_ld * 4, d_out, out_len * 4, out_len * 4, 2,
+                                    cudaMemcpyDeviceToHost, st));
+    return hrir_sync(ctx, stream);
+}
+
+}  // extern "C"

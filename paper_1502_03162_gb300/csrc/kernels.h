@@ -1,0 +1,73 @@
+// kernels.h -- internal launchers of the sm_103a renderer (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace hrir {
+
+// ---- direct-convolution mixing (sparse reflection taps, or dense HRIR) -----------------
+constexpr int kMixR = 36;                         // outputs per lane = window chunk width
+constexpr int kMixWarps = 8;                      // all compute; warp 0 also issues the TMA
+constexpr int kMixTile = kMixWarps * 32 * kMixR;  // 9216 outputs per tile
+constexpr int kMixThreads = kMixWarps * 32;
+constexpr int kMixMaxStages = 4;
+constexpr int kMixBox = 256;                      // TMA box width (elements)
+constexpr int kRunSources = 64;                   // max sources per register accumulation run
+
+enum MixMode : int { MIX_SPARSE = 0, MIX_DENSE = 1 };
+
+struct MixArgs {
+    const void *src;            // [n_src][ld] sources
+    int64_t ld;                 // row stride in elements
+    int64_t len;                // samples per source
+    int n_src;
+    const int32_t *dir;         // [n_src]
+    int n_dirs;
+    const unsigned char *table; // per-direction records (n_dirs + 1, last one silent)
+    int rec_bytes;              // record stride, multiple of 16
+    int nchunk;                 // filter span in window chunks of kMixR
+    int halo;                   // >= nchunk * kMixR samples of history per tile (multiple of 8)
+    int buf_elems;              // per-stage source buffer, multiple of kMixBox
+    int n_tiles;
+    int stages;                 // pipeline depth (2..kMixMaxStages)
+    Partition part;
+    float *partial;             // [n_tiles][slots][2][kMixTile]
+    int slots;
+    int *status;
+};
+
+size_t mix_smem_bytes(int buf_elems, int elem_bytes, int rec_bytes, int stages);
+// tmap: 2-D tiled tensor map over the sources ({len, n_src}, box {kMixBox, 1}, zero fill)
+cudaError_t launch_mix(int mode, int dtype, const CUtensorMap &tmap, const MixArgs &a, int grid,
+                       size_t smem, cudaStream_t st);
+
+// ---- fixed-order reduction of partial slots + optional resonance FIR -------------------
+struct ReduceArgs {
+    const float *partial;
+    int slots;
+    int n_tiles;
+    int tile;
+    Partition part;
+    const float *res;   // [2][res_len] or nullptr for identity
+    int res_len;
+    int64_t out_len;
+    float *out;
+    int64_t out_ld;
+};
+cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
+
+// ---- table builders and top-K -------------------------------------------------------------
+cudaError_t launch_topk(const float *g, int n_rows, int refl_len, int k, uint16_t *idx, float *w,
+                        uint8_t *nnz, cudaStream_t st);
+cudaError_t launch_build_sparse_records(const uint16_t *idx, const float *w, const uint8_t *nnz,
+                                        int n_dirs, int k_max, unsigned char *rec, int rec_bytes,
+                                        cudaStream_t st);
+cudaError_t launch_build_dense_records(const uint16_t *idx, const float *w, const uint8_t *nnz,
+                                       int n_dirs, int k_max, const float *res, int res_len,
+                                       int hrir_len, int padded_len, float *rec, cudaStream_t st);
+
+}  // namespace hrir

@@ -1,0 +1,75 @@
+// reduce_fir.cu -- deterministic mix reduction fused with the resonance FIR (sm_103a).
+//
+//   z_e[m]   = sum over the partial slots of tile(m), in slot order, compensated (Kahan)
+//   out_e[n] = sum_{l < Lf} f_e[l] z_e[n - l]          (the resonance stage of Eq. 2;
+//                                                      identity when no filter is given)
+// Each block produces kBlk outputs of one ear: it first forms z for [n0 - Lf + 1, n0 + kBlk)
+// in shared memory (coalesced partial reads, fixed summation order), then applies the FIR.
+#include "kernels.h"
+
+namespace hrir {
+
+namespace {
+
+constexpr int kBlk = 2048;
+constexpr int kThreads = 256;
+constexpr int kMaxRes = 512;
+
+__global__ void __launch_bounds__(kThreads) reduce_fir_kernel(const ReduceArgs a)
+{
+    __shared__ float zs[kBlk + kMaxRes - 1];
+    __shared__ float fs[kMaxRes];
+    __shared__ int nslots[2];
+    const int e = blockIdx.y;
+    const int64_t n0 = (int64_t)blockIdx.x * kBlk;
+    const int lf = a.res ? a.res_len : 1;
+    const int64_t m_lo = n0 - (lf - 1);
+    const int64_t m_hi = n0 + kBlk;  // exclusive
+    const int64_t z_len = (int64_t)a.n_tiles * a.tile;
+    const int t_lo = (int)((m_lo > 0 ? m_lo : 0) / a.tile);
+    if (threadIdx.x == 0) {
+        nslots[0] = t_lo < a.n_tiles ? a.part.slots(t_lo) : 0;
+        nslots[1] = t_lo + 1 < a.n_tiles ? a.part.slots(t_lo + 1) : 0;
+    }
+    for (int l = threadIdx.x; l < lf; l += kThreads) fs[l] = a.res ? a.res[e * a.res_len + l] : 1.0f;
+    __syncthreads();
+    const int span = (int)(m_hi - m_lo);
+    for (int i = threadIdx.x; i < span; i += kThreads) {
+        const int64_t m = m_lo + i;
+        float sum = 0.f;
+        if (m >= 0 && m < z_len) {
+            const int t = (int)(m / a.tile);
+            const int ns = nslots[t - t_lo];
+            const float *p = a.partial + ((size_t)t * a.slots * 2 + e) * a.tile + (m - (int64_t)t * a.tile);
+            float c = 0.f;
+            for (int j = 0; j < ns; ++j) {
+                const float y = p[(size_t)j * 2 * a.tile] - c;
+                const float tt = sum + y;
+                c = (tt - sum) - y;
+                sum = tt;
+            }
+        }
+        zs[i] = sum;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBlk; i += kThreads) {
+        const int64_t n = n0 + i;
+        if (n >= a.out_len) break;
+        float acc = 0.f;
+        for (int l = 0; l < lf; ++l) acc = fmaf(fs[l], zs[i + lf - 1 - l], acc);
+        a.out[e * a.out_ld + n] = acc;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st)
+{
+    if (a.out_len <= 0) return cudaSuccess;
+    if ((a.res ? a.res_len : 1) > kMaxRes || a.tile < kBlk + kMaxRes) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((a.out_len + kBlk - 1) / kBlk), 2);
+    reduce_fir_kernel<<<grid, kThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace hrir

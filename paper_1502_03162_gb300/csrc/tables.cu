@@ -1,0 +1,186 @@
+// tables.cu -- filter-pack kernels (sm_103a): top-K tap selection, the sparse tap records
+// consumed by the mixing kernel, and the dense HRIRs x = f * g (Eq. 1) for the baselines.
+#include <climits>
+
+#include "kernels.h"
+
+namespace hrir {
+
+namespace {
+
+// ---- top-K: one warp per row ---------------------------------------------------------------
+// Keeps the k largest strictly positive entries (ties -> smaller index), emitted in ascending
+// index order, padded with (0, 0).  Lane l holds the contiguous slice [l*per, (l+1)*per).
+constexpr int kTopkMaxPer = 64;  // refl_len <= 32 * 64 = 2048
+
+__global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, int n_rows,
+                                                   int refl_len, int k, uint16_t *__restrict__ idx,
+                                                   float *__restrict__ w, uint8_t *__restrict__ nnz)
+{
+    const int row = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n_rows) return;
+    const int per = (refl_len + 31) / 32;
+    const int j0 = lane * per;
+    const float *gr = g + (size_t)row * refl_len;
+    float v[kTopkMaxPer];
+#pragma unroll
+    for (int j = 0; j < kTopkMaxPer; ++j) {
+        const int gi = j0 + j;
+        v[j] = (j < per && gi < refl_len) ? gr[gi] : 0.0f;  // 0 is never selected
+    }
+    uint64_t taken = 0;
+    int cnt = 0;
+    for (; cnt < k; ++cnt) {
+        float bv = 0.f;
+        int bi = INT_MAX;
+#pragma unroll
+        for (int j = 0; j < kTopkMaxPer; ++j) {
+            const bool ok = !((taken >> j) & 1ull) && (v[j] > 0.f);
+            if (ok && (bi == INT_MAX || v[j] > bv)) {
+                bv = v[j];
+                bi = j0 + j;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            const bool better = (oi != INT_MAX) && (bi == INT_MAX || ov > bv || (ov == bv && oi < bi));
+            if (better) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (bi == INT_MAX) break;
+        if (bi >= j0 && bi < j0 + per) taken |= 1ull << (bi - j0);
+    }
+    // ascending-index output: lanes hold ascending slices; prefix-count the kept entries
+    const int mine = __popcll(taken);
+    int before = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, before, off);
+        if (lane >= off) before += o;
+    }
+    before -= mine;
+    uint16_t *ri = idx + (size_t)row * k;
+    float *rw = w + (size_t)row * k;
+    int o = before;
+#pragma unroll
+    for (int j = 0; j < kTopkMaxPer; ++j) {
+        if ((taken >> j) & 1ull) {
+            ri[o] = (uint16_t)(j0 + j);
+            rw[o] = v[j];
+            ++o;
+        }
+    }
+    for (int t = cnt + lane; t < k; t += 32) {
+        ri[t] = 0;
+        rw[t] = 0.f;
+    }
+    if (lane == 0) nnz[row] = (uint8_t)cnt;
+}
+
+// ---- sparse records: merge both ears' ascending tap lists into one descending list ------
+__global__ void build_sparse_records_kernel(const uint16_t *__restrict__ idx,
+                                            const float *__restrict__ w,
+                                            const uint8_t *__restrict__ nnz, int n_dirs, int k_max,
+                                            unsigned char *__restrict__ rec, int rec_bytes)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d > n_dirs) return;
+    int4 *hdr = reinterpret_cast<int4 *>(rec + (size_t)d * rec_bytes);
+    int2 *taps = reinterpret_cast<int2 *>(rec + (size_t)d * rec_bytes + 16);
+    if (d == n_dirs) {  // the silent record used for out-of-range direction ids
+        *hdr = make_int4(0, -1, -1, 0);
+        return;
+    }
+    const size_t rl = ((size_t)d * 2 + 0) * k_max, rr = ((size_t)d * 2 + 1) * k_max;
+    int il = (int)nnz[(size_t)d * 2 + 0] - 1, ir = (int)nnz[(size_t)d * 2 + 1] - 1;
+    const int n = il + ir + 2;
+    int max_idx = -1, min_idx = -1;
+    if (il >= 0) {
+        max_idx = idx[rl + il];
+        min_idx = idx[rl];
+    }
+    if (ir >= 0) {
+        max_idx = max(max_idx, (int)idx[rr + ir]);
+        min_idx = min_idx < 0 ? (int)idx[rr] : min(min_idx, (int)idx[rr]);
+    }
+    for (int o = 0; o < n; ++o) {
+        bool take_left;
+        if (il < 0) take_left = false;
+        else if (ir < 0) take_left = true;
+        else take_left = idx[rl + il] >= idx[rr + ir];
+        if (take_left) {
+            taps[o] = make_int2((int)idx[rl + il], __float_as_int(w[rl + il]));
+            --il;
+        } else {
+            taps[o] = make_int2((int)idx[rr + ir] | (1 << 16), __float_as_int(w[rr + ir]));
+            --ir;
+        }
+    }
+    *hdr = make_int4(n, max_idx, min_idx, 0);
+}
+
+// ---- dense HRIRs: x_{d,e}[n] = sum_t w_t f_e[n - idx_t] (Eq. 1), zero padded -------------
+__global__ void build_dense_records_kernel(const uint16_t *__restrict__ idx,
+                                           const float *__restrict__ w,
+                                           const uint8_t *__restrict__ nnz, int n_dirs, int k_max,
+                                           const float *__restrict__ res, int res_len, int hrir_len,
+                                           int padded_len, float *__restrict__ rec)
+{
+    const int64_t total = (int64_t)(n_dirs + 1) * 2 * padded_len;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(i % padded_len);
+        const int64_t de = i / padded_len;
+        const int e = (int)(de % 2);
+        const int d = (int)(de / 2);
+        float acc = 0.f;
+        if (d < n_dirs && n < hrir_len) {
+            const size_t row = ((size_t)d * 2 + e) * k_max;
+            const int k = nnz[(size_t)d * 2 + e];
+            for (int t = 0; t < k; ++t) {
+                const int l = n - (int)idx[row + t];
+                if (l >= 0 && l < res_len) acc = fmaf(w[row + t], res[e * res_len + l], acc);
+            }
+        }
+        rec[i] = acc;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_topk(const float *g, int n_rows, int refl_len, int k, uint16_t *idx, float *w,
+                        uint8_t *nnz, cudaStream_t st)
+{
+    if (n_rows <= 0) return cudaSuccess;
+    if (refl_len > 32 * kTopkMaxPer) return cudaErrorInvalidValue;
+    topk_kernel<<<(n_rows + 3) / 4, 128, 0, st>>>(g, n_rows, refl_len, k, idx, w, nnz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_sparse_records(const uint16_t *idx, const float *w, const uint8_t *nnz,
+                                        int n_dirs, int k_max, unsigned char *rec, int rec_bytes,
+                                        cudaStream_t st)
+{
+    const int n = n_dirs + 1;
+    build_sparse_records_kernel<<<(n + 127) / 128, 128, 0, st>>>(idx, w, nnz, n_dirs, k_max, rec,
+                                                                rec_bytes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_dense_records(const uint16_t *idx, const float *w, const uint8_t *nnz,
+                                       int n_dirs, int k_max, const float *res, int res_len,
+                                       int hrir_len, int padded_len, float *rec, cudaStream_t st)
+{
+    const int64_t total = (int64_t)(n_dirs + 1) * 2 * padded_len;
+    const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    build_dense_records_kernel<<<blocks, 256, 0, st>>>(idx, w, nnz, n_dirs, k_max, res, res_len,
+                                                       hrir_len, padded_len, rec);
+    return cudaGetLastError();
+}
+
+}  // namespace hrir

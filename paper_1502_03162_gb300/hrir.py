@@ -1,0 +1,258 @@
+"""Thin ctypes binding of the C ABI in include/hrir.h (argument marshalling only).
+
+Every function named ``hrir_*`` here calls the C function of the same name in
+``_lib/libhrir.so``; all rendering work runs in that library's CUDA kernels.  There is no
+CPU fallback: importing this module on a machine without the built library, or calling it
+without a CUDA device, raises.
+
+Tensors are torch tensors (device memory and streams only); pointers are passed through
+``data_ptr()`` and streams through ``torch.cuda.Stream.cuda_stream``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhrir.so")
+
+HRIR_OK, HRIR_EINVAL, HRIR_ENOMEM, HRIR_ECUDA, HRIR_ETIMEDOUT, HRIR_EBUSY, HRIR_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6
+HRIR_F32, HRIR_BF16, HRIR_F16 = 0, 1, 2
+HRIR_SPARSE, HRIR_DENSE, HRIR_FFT = 0, 1, 2
+MODES = {"sparse": HRIR_SPARSE, "dense": HRIR_DENSE, "fft": HRIR_FFT}
+STATUS_NAMES = {0: "HRIR_OK", -1: "HRIR_EINVAL", -2: "HRIR_ENOMEM", -3: "HRIR_ECUDA",
+                -4: "HRIR_ETIMEDOUT", -5: "HRIR_EBUSY", -6: "HRIR_ESTATE"}
+
+# every symbol the header declares, with its ctypes signature
+_vp, _i, _i64, _cp = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_char_p
+SIGNATURES = {
+    "hrir_version": ([], _i),
+    "hrir_create": ([ctypes.POINTER(_vp), _i], _i),
+    "hrir_destroy": ([_vp], None),
+    "hrir_last_error": ([_vp], _cp),
+    "hrir_sync": ([_vp, _vp], _i),
+    "hrir_topk_pack": ([_vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp], _i),
+    "hrir_load_filters": ([_vp, _i, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _i], _i),
+    "hrir_out_len": ([_vp, _i64, _i], _i64),
+    "hrir_render_batch": ([_vp, _i, _i64, _i64, _i, _vp, _vp, _i, _i, _vp, _i64, _vp], _i),
+    "hrir_render_batch_host": ([_vp, _i, _i64, _i64, _i, _vp, _vp, _i, _i, _vp, _i64, _vp], _i),
+    "hrir_set_timing": ([_vp, _i], _i),
+    "hrir_kernel_times": ([_vp, _vp, _vp, _i], _i),
+}
+HRIR_K_COUNT = 8
+KERNEL_NAMES = {0: "mix_sparse", 1: "mix_dense", 2: "reduce_fir", 3: "fft", 4: "tables"}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class HRIRError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libhrir.so (built by paper_1502_03162_gb300.build); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is not built; run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            lib = ctypes.CDLL(path)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _check(ctx, rc: int):
+    if rc != HRIR_OK:
+        msg = load_library().hrir_last_error(ctx)
+        raise HRIRError(rc, msg.decode() if msg else "")
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    return {torch.float32: HRIR_F32, torch.bfloat16: HRIR_BF16, torch.float16: HRIR_F16}[t.dtype]
+
+
+# ---------------------------------------------------------------------------------------
+# same-name wrappers
+# ---------------------------------------------------------------------------------------
+def hrir_version() -> int:
+    return load_library().hrir_version()
+
+
+def hrir_create(device: int = 0) -> int:
+    lib = load_library()
+    h = _vp()
+    rc = lib.hrir_create(ctypes.byref(h), device)
+    if rc != HRIR_OK:
+        raise HRIRError(rc, lib.hrir_last_error(None).decode())
+    return h.value
+
+
+def hrir_destroy(ctx) -> None:
+    load_library().hrir_destroy(ctx)
+
+
+def hrir_last_error(ctx) -> str:
+    return load_library().hrir_last_error(ctx).decode()
+
+
+def hrir_sync(ctx, stream=None) -> int:
+    """Returns the status (does not raise) so callers can test device-side flags."""
+    return load_library().hrir_sync(ctx, _stream_handle(stream))
+
+
+def hrir_topk_pack(ctx, g, k: int, idx=None, w=None, nnz=None, stream=None):
+    """g: CUDA float32 [..., refl_len].  Returns (idx, w, nnz) CUDA tensors: idx is int16
+    holding the uint16 indices (all < 2048, so the values read the same), w float32, nnz
+    uint8."""
+    import torch
+    assert g.is_cuda and g.dtype == torch.float32 and g.is_contiguous()
+    refl_len = g.shape[-1]
+    lead = tuple(g.shape[:-1])
+    rows = int(np.prod(lead)) if lead else 1
+    if idx is None:
+        idx = torch.empty(lead + (k,), dtype=torch.int16, device=g.device)   # uint16 payload
+    if w is None:
+        w = torch.empty(lead + (k,), dtype=torch.float32, device=g.device)
+    if nnz is None:
+        nnz = torch.empty(lead, dtype=torch.uint8, device=g.device)
+    rc = load_library().hrir_topk_pack(ctx, rows, refl_len, k, g.data_ptr(), idx.data_ptr(),
+                                       w.data_ptr(), nnz.data_ptr(), _stream_handle(stream))
+    _check(ctx, rc)
+    return idx, w, nnz
+
+
+def hrir_load_filters(ctx, tap_idx, tap_w, tap_nnz, refl_len: int, res, fft_size: int = 0):
+    """Host numpy arrays: tap_idx uint16 [n_dirs][2][k_max], tap_w float32, tap_nnz uint8
+    [n_dirs][2], res float32 [2][Lf]."""
+    tap_idx = np.ascontiguousarray(tap_idx, dtype=np.uint16)
+    tap_w = np.ascontiguousarray(tap_w, dtype=np.float32)
+    tap_nnz = np.ascontiguousarray(tap_nnz, dtype=np.uint8)
+    res = np.ascontiguousarray(res, dtype=np.float32)
+    n_dirs, n_ears, k_max = tap_idx.shape
+    rc = load_library().hrir_load_filters(
+        ctx, n_dirs, n_ears, refl_len, k_max, tap_idx.ctypes.data, tap_w.ctypes.data,
+        tap_nnz.ctypes.data, res.shape[1], res.ctypes.data, fft_size)
+    _check(ctx, rc)
+
+
+def hrir_out_len(ctx, length: int, full: bool = True) -> int:
+    return load_library().hrir_out_len(ctx, length, int(full))
+
+
+def hrir_render_batch(ctx, src, dirs, mode="sparse", full=True, length=None, out=None,
+                      stream=None):
+    """src: CUDA [S][ld] float32/bfloat16/float16; dirs: CUDA int32 [S].
+    Returns out: CUDA float32 [2][out_len] (or the given buffer)."""
+    import torch
+    assert src.is_cuda and src.dim() == 2 and src.stride(1) == 1
+    S, ld = src.shape[0], src.stride(0) if src.shape[0] > 1 else src.shape[1]
+    L = src.shape[1] if length is None else int(length)
+    out_len = hrir_out_len(ctx, L, full)
+    if out is None:
+        out = torch.empty((2, max(out_len, 1)), dtype=torch.float32, device=src.device)
+    assert out.is_cuda and out.dtype == torch.float32 and out.stride(1) == 1
+    assert dirs.is_cuda and dirs.dtype == torch.int32 and dirs.is_contiguous()
+    rc = load_library().hrir_render_batch(
+        ctx, S, L, ld, _dtype_code(src), src.data_ptr(), dirs.data_ptr(),
+        MODES[mode] if isinstance(mode, str) else int(mode), int(full), out.data_ptr(),
+        out.stride(0), _stream_handle(stream))
+    _check(ctx, rc)
+    return out[:, :out_len]
+
+
+def hrir_render_batch_host(ctx, src, dirs, mode="sparse", full=True, length=None, out=None,
+                           stream=None):
+    """src: CPU tensor [S][ld] (pinned for speed); dirs: CPU int32 [S].  Synchronous; returns
+    a CPU float32 [2][out_len] tensor."""
+    import torch
+    assert (not src.is_cuda) and src.dim() == 2 and src.stride(1) == 1
+    S = src.shape[0]
+    ld = src.stride(0) if S > 1 else src.shape[1]
+    L = src.shape[1] if length is None else int(length)
+    out_len = hrir_out_len(ctx, L, full)
+    if out is None:
+        out = torch.empty((2, max(out_len, 1)), dtype=torch.float32,
+                          pin_memory=src.is_pinned())
+    dirs = dirs.contiguous()
+    rc = load_library().hrir_render_batch_host(
+        ctx, S, L, ld, _dtype_code(src), src.data_ptr(), dirs.data_ptr(),
+        MODES[mode] if isinstance(mode, str) else int(mode), int(full), out.data_ptr(),
+        out.stride(0), _stream_handle(stream))
+    _check(ctx, rc)
+    return out[:, :out_len]
+
+
+def hrir_set_timing(ctx, enable: bool) -> None:
+    _check(ctx, load_library().hrir_set_timing(ctx, int(enable)))
+
+
+def hrir_kernel_times(ctx, reset: bool = True):
+    """{kernel family name: (milliseconds, launches)} accumulated since the last reset."""
+    ms = (ctypes.c_double * HRIR_K_COUNT)()
+    n = (ctypes.c_int64 * HRIR_K_COUNT)()
+    _check(ctx, load_library().hrir_kernel_times(ctx, ms, n, int(reset)))
+    return {KERNEL_NAMES.get(i, str(i)): (ms[i], n[i]) for i in range(HRIR_K_COUNT) if n[i]}
+
+
+class Renderer:
+    """Owns one hrir_ctx; convenience layer over the same-name functions above."""
+
+    def __init__(self, device: int = 0):
+        self.ctx = hrir_create(device)
+        self.device = device
+
+    def close(self):
+        if self.ctx:
+            hrir_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_filters(self, tap_idx, tap_w, tap_nnz, refl_len, res, fft_size=0):
+        hrir_load_filters(self.ctx, tap_idx, tap_w, tap_nnz, refl_len, res, fft_size)
+
+    def topk_pack(self, g, k, stream=None):
+        return hrir_topk_pack(self.ctx, g, k, stream=stream)
+
+    def render(self, src, dirs, mode="sparse", full=True, length=None, out=None, stream=None):
+        return hrir_render_batch(self.ctx, src, dirs, mode, full, length, out, stream)
+
+    def render_host(self, src, dirs, mode="sparse", full=True, length=None, out=None,
+                    stream=None):
+        return hrir_render_batch_host(self.ctx, src, dirs, mode, full, length, out, stream)
+
+    def sync(self, stream=None) -> int:
+        return hrir_sync(self.ctx, stream)
+
+    def out_len(self, length, full=True):
+        return hrir_out_len(self.ctx, length, full)
+
+    def set_timing(self, enable=True):
+        hrir_set_timing(self.ctx, enable)
+
+    def kernel_times(self, reset=True):
+        return hrir_kernel_times(self.ctx, reset)

@@ -1,0 +1,59 @@
+"""The C-ABI library loads and exports every symbol include/hrir.h declares (no GPU needed;
+no compute call is made)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hrir.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hrir_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1502_03162_gb300 import build, hrir
+    build.build()
+    return hrir.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("hrir_load_filters", "hrir_render_batch", "hrir_create", "hrir_sync"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1502_03162_gb300 import hrir
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} not exported by libhrir.so"
+        assert name in hrir.SIGNATURES, f"{name} has no Python binding"
+
+
+def test_version_and_cpu_only_create_fails_cleanly(lib):
+    from paper_1502_03162_gb300 import hrir
+    assert hrir.hrir_version() >= 1
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(hrir.HRIRError) as ei:
+        hrir.hrir_create(0)
+    assert ei.value.status == hrir.HRIR_ECUDA
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_1502_03162_gb300 import hrir
+    import importlib
+    mod = importlib.reload(hrir)
+    saved = mod._lib
+    try:
+        mod._lib = None
+        with pytest.raises(RuntimeError):
+            mod.load_library(str(tmp_path / "missing.so"))
+    finally:
+        mod._lib = saved

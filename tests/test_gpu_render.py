@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA rendering path (through the C ABI) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_03162_gb300 import synth
+from tests.gpu_util import TOL, assert_close, tables
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rend():
+    from paper_1502_03162_gb300 import hrir
+    r = hrir.Renderer(0)
+    yield r
+    r.close()
+
+
+def _dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+# ------------------------------------------------------------------------------- top-K pack
+@pytest.mark.parametrize("refl_len", [200, 33, 2048])
+def test_topk_pack_bit_exact(rend, refl_len):
+    rng = np.random.default_rng(100 + refl_len)
+    G = synth.reflection_bank(rng, 64, n_refl=min(60, refl_len), refl_len=refl_len)
+    G[0, 0] = 0
+    G[1, 1] = -1
+    G[2, 0, 5 % refl_len] = np.nan
+    G[3, 0] = 0
+    G[3, 0, [7 % refl_len, 3, 11 % refl_len, 2]] = 0.5
+    G[4, 1, :] = 0.25                                  # all equal: the k smallest indices win
+    G[5, 0, :] = np.float32(1e-42)                     # denormals are positive
+    g = _dev(G)
+    for k in (0, 1, 8, 16, 32, 48, 64):
+        idx, w, nnz = rend.topk_pack(g, k)
+        torch.cuda.synchronize()
+        ri, rw, rn = oracle.topk(G, k)
+        np.testing.assert_array_equal(nnz.cpu().numpy(), rn)
+        np.testing.assert_array_equal(idx.cpu().numpy().astype(np.int64) & 0xFFFF, ri.astype(np.int64))
+        np.testing.assert_array_equal(w.cpu().numpy().view(np.uint32), rw.view(np.uint32))
+
+
+# ------------------------------------------------------------------------------ rendering
+def _render_both(rend, y, dirs, idx, w, nnz, res, modes=("sparse", "dense"), length=None,
+                 dtype=None, refl_len=200):
+    rend.load_filters(idx, w, nnz, refl_len, res)
+    yd = _dev(y, dtype)
+    dd = _dev(dirs.astype(np.int32))
+    outs = {}
+    for m in modes:
+        for full in (True, False):
+            o = rend.render(yd, dd, mode=m, full=full, length=length)
+            assert rend.sync() == 0
+            outs[(m, full)] = o.cpu().numpy()
+    return outs
+
+
+def test_tiny_config_matches_oracle(rend):
+    cfg = synth.tiny_config(seed=1)
+    idx, w, nnz = oracle.topk(cfg["G"], cfg["k"])
+    assert np.all(nnz == 16)
+    ref = oracle.render_sparse(cfg["y"], cfg["dirs"], idx, w, nnz, 200, cfg["res"])
+    outs = _render_both(rend, cfg["y"], cfg["dirs"], idx, w, nnz, cfg["res"])
+    L = cfg["y"].shape[1]
+    for m in ("sparse", "dense"):
+        assert outs[(m, True)].shape == (2, L + 230)
+        assert_close(outs[(m, True)], ref, what=f"tiny {m} full")
+        assert outs[(m, False)].shape == (2, L)
+        assert_close(outs[(m, False)], ref[:, :L], what=f"tiny {m} same")
+
+
+@pytest.mark.parametrize("S,L,k,n_dirs", [(37, 30001, 16, 50), (5, 9216 * 2 - 199, 8, 7),
+                                          (130, 4099, 32, 1250), (3, 200, 16, 3)])
+def test_batched_matches_oracle(rend, S, L, k, n_dirs):
+    rng = np.random.default_rng(S * 7 + L)
+    _, idx, w, nnz, res = tables(rng, n_dirs, k)
+    ld = (L + 7) // 8 * 8 + 8
+    y = np.full((S, ld), np.nan, dtype=np.float32)       # padding must never be read
+    y[:, :L] = synth.sources_ar1(rng, S, L)
+    dirs = synth.directions(rng, S, n_dirs)
+    ref = oracle.render_sparse(y, dirs, idx, w, nnz, 200, res, length=L)
+    outs = _render_both(rend, y, dirs, idx, w, nnz, res, length=L)
+    for m in ("sparse", "dense"):
+        assert np.isfinite(outs[(m, True)]).all()
+        assert_close(outs[(m, True)], ref, what=f"{m} S={S} L={L}")
+        assert_close(outs[(m, False)], ref[:, :L], what=f"{m} same S={S} L={L}")
+
+
+def test_edge_cases(rend):
+    rng = np.random.default_rng(5)
+    _, idx, w, nnz, res = tables(rng, 4, 16)
+    nnz = nnz.copy()
+    nnz[3] = 0                                           # a direction with no taps
+    rend.load_filters(idx, w, nnz, 200, res)
+    for L in (1, 3, 7, 199, 200, 201, 9216, 9217):
+        y = rng.standard_normal((6, (L + 7) // 8 * 8)).astype(np.float32)
+        dirs = np.array([0, 1, 2, 3, 0, 3], np.int32)
+        ref = oracle.render_sparse(y, dirs, idx, w, nnz, 200, res, length=L)
+        for m in ("sparse", "dense"):
+            o = rend.render(_dev(y), _dev(dirs), mode=m, length=L).cpu().numpy()
+            assert rend.sync() == 0
+            assert_close(o, ref, what=f"{m} L={L}")
+    # silent direction only -> exact zeros
+    y = rng.standard_normal((2, 64)).astype(np.float32)
+    o = rend.render(_dev(y), _dev(np.array([3, 3], np.int32))).cpu().numpy()
+    assert not o.any()
+    # no sources -> zeros of full length; empty sources -> empty output
+    o = rend.render(_dev(np.zeros((0, 64), np.float32)), _dev(np.zeros(0, np.int32)), length=64)
+    assert o.shape == (2, 64 + 230) and not o.cpu().numpy().any()
+    o = rend.render(_dev(y), _dev(np.array([0, 1], np.int32)), length=0)
+    assert o.shape[1] == 0
+
+
+def test_bad_direction_is_silent_and_flagged(rend):
+    from paper_1502_03162_gb300 import hrir
+    rng = np.random.default_rng(6)
+    _, idx, w, nnz, res = tables(rng, 4, 16)
+    rend.load_filters(idx, w, nnz, 200, res)
+    y = rng.standard_normal((3, 1000)).astype(np.float32)
+    o = rend.render(_dev(y), _dev(np.array([1, 9, -2], np.int32))).cpu().numpy()
+    assert rend.sync() == hrir.HRIR_EINVAL
+    assert rend.sync() == 0                              # flag cleared
+    ref = oracle.render_sparse(y[:1], np.array([1], np.int32), idx, w, nnz, 200, res)
+    assert_close(o, ref, what="bad dirs")
+
+
+def test_invalid_arguments_rejected(rend):
+    from paper_1502_03162_gb300 import hrir
+    rng = np.random.default_rng(7)
+    _, idx, w, nnz, res = tables(rng, 4, 16)
+    bad_idx = idx.copy()
+    bad_idx[0, 0, :2] = [5, 5]
+    with pytest.raises(hrir.HRIRError):
+        rend.load_filters(bad_idx, w, nnz, 200, res)
+    bad_w = w.copy()
+    bad_w[1, 1, 0] = -1.0
+    with pytest.raises(hrir.HRIRError):
+        rend.load_filters(idx, bad_w, nnz, 200, res)
+    rend.load_filters(idx, w, nnz, 200, res)
+    y = torch.zeros((2, 1001), device="cuda")            # row stride not a multiple of 16 bytes
+    with pytest.raises(hrir.HRIRError):
+        rend.render(y, _dev(np.zeros(2, np.int32)))
+
+
+@pytest.mark.parametrize("dt", ["bfloat16", "float16"])
+def test_16bit_sources(rend, dt):
+    rng = np.random.default_rng(8)
+    _, idx, w, nnz, res = tables(rng, 40, 16)
+    S, L = 70, 20011
+    ld = (L + 7) // 8 * 8
+    y = np.zeros((S, ld), np.float32)
+    y[:, :L] = synth.sources_ar1(rng, S, L)
+    tdt = getattr(torch, dt)
+    yq = torch.from_numpy(y).to(tdt)
+    ydq = yq.float().numpy()                             # the values the kernel sees
+    dirs = synth.directions(rng, S, 40)
+    ref = oracle.render_sparse(ydq, dirs, idx, w, nnz, 200, res, length=L)
+    rend.load_filters(idx, w, nnz, 200, res)
+    for m in ("sparse", "dense"):
+        o = rend.render(yq.cuda(), _dev(dirs), mode=m, length=L).cpu().numpy()
+        assert rend.sync() == 0
+        assert_close(o, ref, what=f"{dt} {m}")
+
+
+def test_deterministic_and_host_path(rend):
+    rng = np.random.default_rng(9)
+    _, idx, w, nnz, res = tables(rng, 30, 16)
+    S, L = 300, 12345
+    y = np.zeros((S, 12352), np.float32)
+    y[:, :L] = synth.sources_ar1(rng, S, L)
+    dirs = synth.directions(rng, S, 30)
+    rend.load_filters(idx, w, nnz, 200, res)
+    yd, dd = _dev(y), _dev(dirs)
+    a = rend.render(yd, dd, length=L).cpu().numpy()
+    b = rend.render(yd, dd, length=L).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    h = rend.render_host(torch.from_numpy(y).pin_memory(), torch.from_numpy(dirs), length=L)
+    np.testing.assert_array_equal(h.numpy(), a)
+    ref = oracle.render_sparse(y, dirs, idx, w, nnz, 200, res, length=L)
+    assert_close(a, ref, what="S=300")
+
+
+@pytest.mark.parametrize("k", [8, 16, 32])
+def test_full_size_batched_config_sampled(rend, k):
+    """1024 sources x 480000 samples (10 s at 48 kHz), 1250 directions: the launch the
+    benchmark times, checked at sampled output positions computed one by one."""
+    cfg = synth.batched_config(S=1024, L=480000, seed=2)
+    G = torch.from_numpy(cfg["G"]).cuda()
+    idx_d, w_d, nnz_d = rend.topk_pack(G, k)
+    idx = (idx_d.cpu().numpy().astype(np.int64) & 0xFFFF).astype(np.uint16)
+    w, nnz = w_d.cpu().numpy(), nnz_d.cpu().numpy()
+    ri, rw, rn = oracle.topk(cfg["G"], k)
+    np.testing.assert_array_equal(idx, ri)
+    np.testing.assert_array_equal(w.view(np.uint32), rw.view(np.uint32))
+    rend.load_filters(idx, w, nnz, 200, cfg["res"])
+    y = cfg["y"]
+    L = y.shape[1]
+    out = {}
+    for m in ("sparse", "dense"):
+        o = rend.render(torch.from_numpy(y).cuda(), _dev(cfg["dirs"]), mode=m)
+        assert rend.sync() == 0
+        out[m] = o.cpu().numpy()
+        assert out[m].shape == (2, L + 230) and np.isfinite(out[m]).all()
+    rng = np.random.default_rng(77)
+    pos = np.unique(np.concatenate([[0, 1, 199, 230, 9215, 9216, L - 1, L, L + 198, L + 229],
+                                    rng.integers(0, L + 230, 40)]))
+    ref = oracle.render_at(y, cfg["dirs"], idx, w, nnz, 200, cfg["res"], pos)
+    # tolerance scale: RMS of the whole GPU output (the oracle has only samples)
+    for m in ("sparse", "dense"):
+        rms = np.sqrt(np.mean(out[m].astype(np.float64) ** 2, axis=1))
+        err = np.max(np.abs(out[m][:, pos] - ref), axis=1)
+        assert np.all(err <= TOL * rms), f"{m} K={k}: err {err} rms {rms}"

@@ -186,6 +186,20 @@ def test_render_three_ways_agree_and_are_linear_in_sources():
     assert np.max(np.abs(singles - a)) < 1e-12 * scale
 
 
+def test_render_at_equals_full_render():
+    rng = np.random.default_rng(11)
+    idx, w, nnz, res = _tables(rng, 6, 12)
+    S, L = 5, 400
+    y = rng.standard_normal((S, L)).astype(np.float32)
+    dirs = rng.integers(0, 6, S).astype(np.int32)
+    full = oracle.render_sparse(y, dirs, idx, w, nnz, 200, res)
+    pos = np.array([0, 1, 17, 199, 230, 399, 400, 628, 629, 630, -1, 10_000])
+    at = oracle.render_at(y, dirs, idx, w, nnz, 200, res, pos)
+    inside = (pos >= 0) & (pos < full.shape[1])
+    assert np.max(np.abs(at[:, inside] - full[:, pos[inside]])) < 1e-12 * np.max(np.abs(full))
+    assert not at[:, ~inside].any()
+
+
 def test_render_edge_cases():
     rng = np.random.default_rng(8)
     idx, w, nnz, res = _tables(rng, 2, 4)
