@@ -23,7 +23,7 @@ struct hrir_ctx {
     bool loaded = false;
     int n_dirs = 0, refl_len = 0, k_max = 0, res_len = 0, hrir_len = 0, fft_size = 0;
     unsigned char *d_sparse = nullptr;  // (n_dirs + 1) sparse tap records
-    int sparse_rec_bytes = 0, sparse_nchunk = 0;
+    int sparse_rec_bytes = 0, sparse_nchunk = 0, sparse_nch_pad = 0;
     float *d_dense = nullptr;           // (n_dirs + 1) x [2][dense_padded]
     int dense_padded = 0, dense_nchunk = 0;
     float *d_res = nullptr;             // [2][res_len]
@@ -351,9 +351,11 @@ int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k
     uint16_t *d_idx = nullptr;
     float *d_w = nullptr;
     uint8_t *d_nnz = nullptr;
-    const int sparse_rec = (int)round_up(16 + 2 * (int64_t)k_max * 8, 16);
-    const int dense_nchunk = (hrir_len + kMixR - 1) / kMixR;
-    const int dense_padded = dense_nchunk * kMixR;
+    const int sparse_nchunk = (refl_len + kSparseR - 1) / kSparseR;
+    const int sparse_nch_pad = (int)round_up(sparse_nchunk, 8);
+    const int sparse_rec = (int)round_up(16 + 2 * sparse_nch_pad + 2 * (int64_t)k_max * 8, 16);
+    const int dense_nchunk = (hrir_len + kDenseR - 1) / kDenseR;
+    const int dense_padded = dense_nchunk * kDenseR;
     int rc = HRIR_OK;
     cudaError_t e = cudaSuccess;
     do {
@@ -372,8 +374,9 @@ int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k
         if ((e = cudaMemcpy(ctx->d_res, resonance, 2 * (size_t)res_len * 4, cudaMemcpyHostToDevice)) !=
             cudaSuccess)
             break;
-        if ((e = launch_build_sparse_records(d_idx, d_w, d_nnz, n_dirs, (int)kk, ctx->d_sparse,
-                                             sparse_rec, 0)) != cudaSuccess)
+        if ((e = launch_build_sparse_records(d_idx, d_w, d_nnz, n_dirs, (int)kk, kSparseR,
+                                             sparse_nch_pad, ctx->d_sparse, sparse_rec, 0)) !=
+            cudaSuccess)
             break;
         if ((e = launch_build_dense_records(d_idx, d_w, d_nnz, n_dirs, (int)kk, ctx->d_res, res_len,
                                             hrir_len, dense_padded, ctx->d_dense, 0)) != cudaSuccess)
@@ -397,7 +400,8 @@ int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k
     ctx->hrir_len = hrir_len;
     ctx->fft_size = fft_size;
     ctx->sparse_rec_bytes = sparse_rec;
-    ctx->sparse_nchunk = (refl_len + kMixR - 1) / kMixR;
+    ctx->sparse_nchunk = sparse_nchunk;
+    ctx->sparse_nch_pad = sparse_nch_pad;
     ctx->dense_nchunk = dense_nchunk;
     ctx->dense_padded = dense_padded;
     ctx->loaded = true;
@@ -441,11 +445,13 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
 
     const bool sparse = mode == HRIR_SPARSE;
     const int nchunk = sparse ? ctx->sparse_nchunk : ctx->dense_nchunk;
-    const int halo = (int)round_up((int64_t)nchunk * kMixR, 8);
-    const int buf_elems = (int)round_up(halo + kMixTile, kMixBox);
+    const MixShape shape = mix_shape(sparse ? MIX_SPARSE : MIX_DENSE);
+    const int tile = shape.tile;
+    const int halo = (int)round_up((int64_t)nchunk * shape.r, 8);
+    const int buf_elems = (int)round_up(halo + tile, kMixBox);
     const int rec_bytes = sparse ? ctx->sparse_rec_bytes : 2 * ctx->dense_padded * 4;
     const int64_t mix_len = sparse ? std::min<int64_t>(out_len, len + ctx->refl_len - 1) : out_len;
-    const int n_tiles = (int)((mix_len + kMixTile - 1) / kMixTile);
+    const int n_tiles = (int)((mix_len + tile - 1) / tile);
     size_t smem = 0;
     const int stages = pick_stages(buf_elems, (int)es, rec_bytes, &smem);
     if (stages == 0) return fail(ctx, HRIR_EINVAL, "filters too long for the shared-memory pipeline");
@@ -460,7 +466,7 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
     part.gs = kRunSources;
     int slots = 0;
     for (int t = 0; t < n_tiles; ++t) slots = std::max(slots, part.slots(t));
-    const size_t pbytes = (size_t)n_tiles * slots * 2 * kMixTile * sizeof(float);
+    const size_t pbytes = (size_t)n_tiles * slots * 2 * tile * sizeof(float);
     rc = grow(ctx, (void **)&ctx->d_partial, &ctx->partial_bytes, pbytes);
     if (rc) return rc;
 
@@ -473,7 +479,7 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
     a.n_dirs = ctx->n_dirs;
     a.table = sparse ? ctx->d_sparse : reinterpret_cast<const unsigned char *>(ctx->d_dense);
     a.rec_bytes = rec_bytes;
-    a.nchunk = nchunk;
+    a.nchunk = sparse ? ctx->sparse_nch_pad : nchunk;
     a.halo = halo;
     a.buf_elems = buf_elems;
     a.n_tiles = n_tiles;
@@ -492,7 +498,7 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
     r.partial = ctx->d_partial;
     r.slots = slots;
     r.n_tiles = n_tiles;
-    r.tile = kMixTile;
+    r.tile = tile;
     r.part = part;
     r.res = sparse ? ctx->d_res : nullptr;
     r.res_len = ctx->res_len;

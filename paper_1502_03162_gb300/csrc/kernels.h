@@ -10,10 +10,23 @@
 namespace hrir {
 
 // ---- direct-convolution mixing (sparse reflection taps, or dense HRIR) -----------------
-constexpr int kMixR = 36;                         // outputs per lane = window chunk width
-constexpr int kMixWarps = 8;                      // all compute; warp 0 also issues the TMA
-constexpr int kMixTile = kMixWarps * 32 * kMixR;  // 9216 outputs per tile
-constexpr int kMixThreads = kMixWarps * 32;
+// Outputs per lane (= window chunk width) and warps per CTA of each mixing kernel.  All warps
+// compute; warp 0 also issues the TMA loads.  The tile is warps x 32 lanes x R outputs.
+#ifndef HRIR_SPARSE_R
+#define HRIR_SPARSE_R 20
+#endif
+#ifndef HRIR_SPARSE_WARPS
+#define HRIR_SPARSE_WARPS 16
+#endif
+#ifndef HRIR_DENSE_R
+#define HRIR_DENSE_R 36
+#endif
+#ifndef HRIR_DENSE_WARPS
+#define HRIR_DENSE_WARPS 8
+#endif
+constexpr int kSparseR = HRIR_SPARSE_R, kSparseWarps = HRIR_SPARSE_WARPS;
+constexpr int kDenseR = HRIR_DENSE_R, kDenseWarps = HRIR_DENSE_WARPS;
+constexpr int kMixMaxR = 36;
 constexpr int kMixMaxStages = 4;
 constexpr int kMixBox = 256;                      // TMA box width (elements)
 constexpr int kRunSources = 64;                   // max sources per register accumulation run
@@ -29,17 +42,22 @@ struct MixArgs {
     int n_dirs;
     const unsigned char *table; // per-direction records (n_dirs + 1, last one silent)
     int rec_bytes;              // record stride, multiple of 16
-    int nchunk;                 // filter span in window chunks of kMixR
-    int halo;                   // >= nchunk * kMixR samples of history per tile (multiple of 8)
+    int nchunk;                 // filter span in window chunks of R (sparse: per-chunk
+                                // count array length, padded to a multiple of 8)
+    int halo;                   // >= nchunk * R samples of history per tile (multiple of 8)
     int buf_elems;              // per-stage source buffer, multiple of kMixBox
     int n_tiles;
     int stages;                 // pipeline depth (2..kMixMaxStages)
     Partition part;
-    float *partial;             // [n_tiles][slots][2][kMixTile]
+    float *partial;             // [n_tiles][slots][2][tile]
     int slots;
     int *status;
 };
 
+struct MixShape {
+    int r, warps, tile;
+};
+MixShape mix_shape(int mode);
 size_t mix_smem_bytes(int buf_elems, int elem_bytes, int rec_bytes, int stages);
 // tmap: 2-D tiled tensor map over the sources ({len, n_src}, box {kMixBox, 1}, zero fill)
 cudaError_t launch_mix(int mode, int dtype, const CUtensorMap &tmap, const MixArgs &a, int grid,
@@ -64,8 +82,8 @@ cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
 cudaError_t launch_topk(const float *g, int n_rows, int refl_len, int k, uint16_t *idx, float *w,
                         uint8_t *nnz, cudaStream_t st);
 cudaError_t launch_build_sparse_records(const uint16_t *idx, const float *w, const uint8_t *nnz,
-                                        int n_dirs, int k_max, unsigned char *rec, int rec_bytes,
-                                        cudaStream_t st);
+                                        int n_dirs, int k_max, int R, int nch_pad,
+                                        unsigned char *rec, int rec_bytes, cudaStream_t st);
 cudaError_t launch_build_dense_records(const uint16_t *idx, const float *w, const uint8_t *nnz,
                                        int n_dirs, int k_max, const float *res, int res_len,
                                        int hrir_len, int padded_len, float *rec, cudaStream_t st);

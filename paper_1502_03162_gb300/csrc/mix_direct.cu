@@ -11,32 +11,31 @@
 //    with 2-D tensor TMA boxes (cp.async.bulk.tensor + mbarrier complete_tx; samples
 //    outside [0, len) arrive as hardware zero fill), plus the direction's filter record
 //    as a 1-D bulk copy in the same stage;
-//  * all eight warps compute; each owns 32 lanes x R = 36 consecutive outputs per lane and keeps
+//  * all warps compute; each owns 32 lanes x R consecutive outputs per lane and keeps
 //    a 2R-sample register window of the source: for filter taps with offsets in chunk c,
 //    [cR, cR + R), output n + r needs y[n + r - cR - delta] = win[R - delta + r], a fixed
-//    register for each (delta, r).  A warp-uniform switch on (ear, delta) picks the code
-//    path, so each tap costs R FMAs with no shared-memory traffic; moving to the next
+//    register for each (delta, r).  A warp-uniform indirect jump on (ear, delta) picks the
+//    code path, so each tap costs R FMAs with no shared-memory traffic; moving to the next
 //    chunk reuses half the window and loads R fresh samples (conflict-free LDS.128: the
-//    lane stride of 36 floats is an odd number of 16-byte bank groups);
+//    lane stride of R floats is an odd number of 16-byte bank groups);
 //  * register accumulators are flushed every <= 64 sources into partial slots that the
 //    reduction kernel sums in a fixed order (deterministic, bounded FP32 error).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "kernels.h"
+#include "tap_dispatch.cuh"
 
 namespace hrir {
 
 namespace {
 
-constexpr int R = kMixR;
-
 // ---- window loads (R consecutive samples, widened to FP32) -------------------------------
-template <typename T>
+template <typename T, int R>
 struct Window;
 
-template <>
-struct Window<float> {
+template <int R>
+struct Window<float, R> {
     static __device__ __forceinline__ void load(const float *p, float (&v)[R])
     {
         const float4 *q = reinterpret_cast<const float4 *>(p);
@@ -51,8 +50,8 @@ struct Window<float> {
     }
 };
 
-template <>
-struct Window<__nv_bfloat16> {
+template <int R>
+struct Window<__nv_bfloat16, R> {
     static __device__ __forceinline__ void load(const __nv_bfloat16 *p, float (&v)[R])
     {
         const uint2 *q = reinterpret_cast<const uint2 *>(p);
@@ -67,8 +66,8 @@ struct Window<__nv_bfloat16> {
     }
 };
 
-template <>
-struct Window<__half> {
+template <int R>
+struct Window<__half, R> {
     static __device__ __forceinline__ void load(const __half *p, float (&v)[R])
     {
         const uint2 *q = reinterpret_cast<const uint2 *>(p);
@@ -85,88 +84,48 @@ struct Window<__half> {
     }
 };
 
-// ---- one tap of the sparse filter: acc[r] += w * y[n + r - (cR + D)] ----------------------
-template <int D>
-__device__ __forceinline__ void tap(const float (&lo)[R], const float (&hi)[R], float (&acc)[R],
-                                    float w)
-{
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        constexpr int kBase = R - D;
-        const float v = (kBase + r < R) ? lo[(kBase + r) % R] : hi[(kBase + r - R) % R];
-        acc[r] = fmaf(w, v, acc[r]);
-    }
-}
+// ---- taps of the sparse filter: acc[r] += w * y[n + r - (cR + delta)] --------------------
+// With lo = y[n - (c+1)R .. n - cR) and hi = y[n - cR .. n - cR + R), the sample for output
+// r is window index R - delta + r.  TapChunk<R> (generated inline PTX) runs all taps of a
+// chunk, one brx.idx.uni jump per tap into 2R straight-line FMA blocks.
 
-#define HRIR_CASE(D)                    \
-    case D:                             \
-        tap<D>(lo, hi, accL, w);        \
-        break;                          \
-    case R + D:                         \
-        tap<D>(lo, hi, accR, w);        \
-        break;
-#define HRIR_CASE4(D) HRIR_CASE(D) HRIR_CASE(D + 1) HRIR_CASE(D + 2) HRIR_CASE(D + 3)
-
-__device__ __forceinline__ void dispatch_tap(int code, float w, const float (&lo)[R],
-                                             const float (&hi)[R], float (&accL)[R],
-                                             float (&accR)[R])
-{
-    static_assert(R == 36, "dispatch table is written out for R = 36");
-    switch (code) {
-        HRIR_CASE4(0)
-        HRIR_CASE4(4)
-        HRIR_CASE4(8)
-        HRIR_CASE4(12)
-        HRIR_CASE4(16)
-        HRIR_CASE4(20)
-        HRIR_CASE4(24)
-        HRIR_CASE4(28)
-        HRIR_CASE4(32)
-        default:
-            break;
-    }
-}
-#undef HRIR_CASE4
-#undef HRIR_CASE
-
-// Sparse record: int4 {n_taps, max_idx, min_idx, 0}, then n_taps int2 {idx | ear << 16,
-// weight bits}, sorted by descending idx.
-template <typename T>
-__device__ __forceinline__ void sparse_source(const T *yb, int halo, int lane_off,
+// Sparse record (built for chunks of R offsets): int4 {n_taps, c_top, c_bot, 0}, u16
+// cnt[nch_pad], then int2 {code, weight bits} per tap in descending chunk order.  The window
+// slides from chunk c_top down to c_bot (later in time); the two halves swap roles each step
+// (A/B ping-pong), so only the R fresh samples are loaded and nothing is moved.
+template <typename T, int R>
+__device__ __forceinline__ void sparse_source(const T *yb, int halo, int lane_off, int nch_pad,
                                               const unsigned char *rec, float (&accL)[R],
                                               float (&accR)[R])
 {
     const int4 hdr = *reinterpret_cast<const int4 *>(rec);
-    const int n_taps = hdr.x;
-    if (n_taps <= 0) return;
-    const int2 *taps = reinterpret_cast<const int2 *>(rec + 16);
-    int c = hdr.y / R;
-    const int c_min = hdr.z / R;
+    if (hdr.x <= 0) return;
+    const uint16_t *cnt = reinterpret_cast<const uint16_t *>(rec + 16);
+    uint32_t taps = smem_addr(rec + 16 + 2 * nch_pad);
+    int c = hdr.y;
+    const int c_bot = hdr.z;
     const T *base = yb + halo + lane_off;
-    float lo[R], hi[R];
-    Window<T>::load(base - (c + 1) * R, lo);
-    Window<T>::load(base - c * R, hi);
-    int ti = 0;
+    float A[R], B[R];
+    Window<T, R>::load(base - (c + 1) * R, A);
+    Window<T, R>::load(base - c * R, B);
     while (true) {
-        const int cb = c * R;
-        while (ti < n_taps) {
-            const int2 tp = taps[ti];
-            const int idx = tp.x & 0xffff;
-            if (idx < cb) break;
-            const int code = (idx - cb) + ((tp.x >> 16) & 1) * R;
-            dispatch_tap(code, __int_as_float(tp.y), lo, hi, accL, accR);
-            ++ti;
-        }
-        if (c <= c_min) break;
+        int n = cnt[c];
+        if (n) TapChunk<R>::run(A, B, accL, accR, taps, n);
+        taps += 8u * n;
+        if (c == c_bot) break;
         --c;
-#pragma unroll
-        for (int i = 0; i < R; ++i) lo[i] = hi[i];
-        Window<T>::load(base - c * R, hi);
+        Window<T, R>::load(base - c * R, A);
+        n = cnt[c];
+        if (n) TapChunk<R>::run(B, A, accL, accR, taps, n);
+        taps += 8u * n;
+        if (c == c_bot) break;
+        --c;
+        Window<T, R>::load(base - c * R, B);
     }
 }
 
 // Dense record: float h[2][nchunk * R] (the HRIR of each ear, zero padded).
-template <typename T>
+template <typename T, int R>
 __device__ __forceinline__ void dense_source(const T *yb, int halo, int lane_off, int nchunk,
                                              const float *h, float (&accL)[R], float (&accR)[R])
 {
@@ -174,8 +133,8 @@ __device__ __forceinline__ void dense_source(const T *yb, int halo, int lane_off
     int c = nchunk - 1;
     const T *base = yb + halo + lane_off;
     float lo[R], hi[R];
-    Window<T>::load(base - (c + 1) * R, lo);
-    Window<T>::load(base - c * R, hi);
+    Window<T, R>::load(base - (c + 1) * R, lo);
+    Window<T, R>::load(base - c * R, hi);
     while (true) {
         const float *hl = h + c * R;
         const float *hr = h + hp + c * R;
@@ -194,7 +153,7 @@ __device__ __forceinline__ void dense_source(const T *yb, int halo, int lane_off
         --c;
 #pragma unroll
         for (int i = 0; i < R; ++i) lo[i] = hi[i];
-        Window<T>::load(base - c * R, hi);
+        Window<T, R>::load(base - c * R, hi);
     }
 }
 
@@ -204,11 +163,11 @@ __device__ __forceinline__ void dense_source(const T *yb, int halo, int lane_off
 template <typename T>
 __device__ __forceinline__ void issue_unit(const CUtensorMap *tmap, const MixArgs &a, int64_t u,
                                            int d, T *ybuf, unsigned char *rbuf, uint32_t full_bar,
-                                           int lane)
+                                           int lane, int tile)
 {
     const int t = (int)(u / a.n_src);
     const int s = (int)(u - (int64_t)t * a.n_src);
-    const int x0 = t * kMixTile - a.halo;
+    const int x0 = t * tile - a.halo;
     const int n_box = a.buf_elems / kMixBox;
     if (lane == 0)
         mbar_arrive_expect_tx(full_bar, (uint32_t)(a.buf_elems * sizeof(T) + a.rec_bytes));
@@ -232,10 +191,11 @@ __device__ __forceinline__ int unit_dir(const MixArgs &a, int64_t u, int lane)
     return d;
 }
 
-template <int MODE, typename T>
-__global__ void __launch_bounds__(kMixThreads, 1)
+template <int MODE, typename T, int R, int NW>
+__global__ void __launch_bounds__(NW * 32, 1)
     mix_kernel(const __grid_constant__ CUtensorMap tmap, const MixArgs a)
 {
+    constexpr int kTile = NW * 32 * R;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int stages = a.stages;
     T *ybuf = reinterpret_cast<T *>(smem);
@@ -248,7 +208,7 @@ __global__ void __launch_bounds__(kMixThreads, 1)
         prefetch_tensormap(&tmap);
         for (int i = 0; i < stages; ++i) {
             mbar_init(smem_addr(&bars[i]), 1);                   // full: producer + tx bytes
-            mbar_init(smem_addr(&bars[stages + i]), kMixWarps);  // empty: one arrive per warp
+            mbar_init(smem_addr(&bars[stages + i]), NW);  // empty: one arrive per warp
         }
         *abort_flag = 0;
         mbar_fence_init();
@@ -267,13 +227,14 @@ __global__ void __launch_bounds__(kMixThreads, 1)
         for (int64_t i = 0; i < n0; ++i) {
             const int d = unit_dir(a, u_begin + i, lane);
             issue_unit<T>(&tmap, a, u_begin + i, d, ybuf + (size_t)i * a.buf_elems,
-                          rbuf + (size_t)i * a.rec_bytes, smem_addr(&bars[i]), lane);
+                          rbuf + (size_t)i * a.rec_bytes, smem_addr(&bars[i]), lane, kTile);
         }
         issued = n0;
         if (issued < n_units) next_dir = unit_dir(a, u_begin + issued, lane);
     }
 
     const int lane_off = (warp * 32 + lane) * R;
+    static_assert(R % 4 == 0 && ((R / 4) & 1), "lane stride must be an odd number of 16-byte groups");
     float accL[R], accR[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) accL[i] = accR[i] = 0.f;
@@ -287,7 +248,7 @@ __global__ void __launch_bounds__(kMixThreads, 1)
             const uint32_t par = (uint32_t)(((k - 1) / stages) & 1);
             if (!mbar_wait_bounded(smem_addr(&bars[stages + st]), par, abort_flag, a.status)) break;
             issue_unit<T>(&tmap, a, u_begin + issued, next_dir, ybuf + (size_t)st * a.buf_elems,
-                          rbuf + (size_t)st * a.rec_bytes, smem_addr(&bars[st]), lane);
+                          rbuf + (size_t)st * a.rec_bytes, smem_addr(&bars[st]), lane, kTile);
             ++issued;
             if (issued < n_units) next_dir = unit_dir(a, u_begin + issued, lane);
         }
@@ -303,19 +264,19 @@ __global__ void __launch_bounds__(kMixThreads, 1)
             break;
         const T *yb = ybuf + (size_t)st * a.buf_elems;
         const unsigned char *rec = rbuf + (size_t)st * a.rec_bytes;
-        if (MODE == MIX_SPARSE)
-            sparse_source<T>(yb, a.halo, lane_off, rec, accL, accR);
+        if constexpr (MODE == MIX_SPARSE)
+            sparse_source<T, R>(yb, a.halo, lane_off, a.nchunk, rec, accL, accR);
         else
-            dense_source<T>(yb, a.halo, lane_off, a.nchunk, reinterpret_cast<const float *>(rec),
-                            accL, accR);
+            dense_source<T, R>(yb, a.halo, lane_off, a.nchunk, reinterpret_cast<const float *>(rec),
+                               accL, accR);
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&bars[stages + st]));
         ++run_n;
         const bool tile_end = (u + 1 == u_end) || ((u + 1) / a.n_src != t);
         if (run_n == a.part.gs || tile_end) {
-            float *p = a.partial + ((size_t)t * a.slots + slot) * 2 * kMixTile + lane_off;
+            float *p = a.partial + ((size_t)t * a.slots + slot) * 2 * kTile + lane_off;
             float4 *pl = reinterpret_cast<float4 *>(p);
-            float4 *pr = reinterpret_cast<float4 *>(p + kMixTile);
+            float4 *pr = reinterpret_cast<float4 *>(p + kTile);
 #pragma unroll
             for (int i = 0; i < R / 4; ++i) {
                 pl[i] = make_float4(accL[4 * i], accL[4 * i + 1], accL[4 * i + 2], accL[4 * i + 3]);
@@ -346,28 +307,38 @@ size_t mix_smem_bytes(int buf_elems, int elem_bytes, int rec_bytes, int stages)
     return (size_t)stages * ((size_t)buf_elems * elem_bytes + rec_bytes) + 2 * stages * 8 + 16;
 }
 
-template <int MODE, typename T>
+MixShape mix_shape(int mode)
+{
+    if (mode == MIX_SPARSE) return {kSparseR, kSparseWarps, kSparseR * kSparseWarps * 32};
+    return {kDenseR, kDenseWarps, kDenseR * kDenseWarps * 32};
+}
+
+template <int MODE, typename T, int R, int NW>
 static cudaError_t launch_one(const CUtensorMap &tmap, const MixArgs &a, int grid, size_t smem,
                               cudaStream_t st)
 {
-    auto k = mix_kernel<MODE, T>;
+    auto k = mix_kernel<MODE, T, R, NW>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, kMixThreads, smem, st>>>(tmap, a);
+    k<<<grid, NW * 32, smem, st>>>(tmap, a);
     return cudaGetLastError();
+}
+
+template <int MODE, int R, int NW>
+static cudaError_t launch_dtype(int dtype, const CUtensorMap &tmap, const MixArgs &a, int grid,
+                                size_t smem, cudaStream_t st)
+{
+    if (dtype == 0) return launch_one<MODE, float, R, NW>(tmap, a, grid, smem, st);
+    if (dtype == 1) return launch_one<MODE, __nv_bfloat16, R, NW>(tmap, a, grid, smem, st);
+    return launch_one<MODE, __half, R, NW>(tmap, a, grid, smem, st);
 }
 
 cudaError_t launch_mix(int mode, int dtype, const CUtensorMap &tmap, const MixArgs &a, int grid,
                        size_t smem, cudaStream_t st)
 {
-    if (mode == MIX_SPARSE) {
-        if (dtype == 0) return launch_one<MIX_SPARSE, float>(tmap, a, grid, smem, st);
-        if (dtype == 1) return launch_one<MIX_SPARSE, __nv_bfloat16>(tmap, a, grid, smem, st);
-        return launch_one<MIX_SPARSE, __half>(tmap, a, grid, smem, st);
-    }
-    if (dtype == 0) return launch_one<MIX_DENSE, float>(tmap, a, grid, smem, st);
-    if (dtype == 1) return launch_one<MIX_DENSE, __nv_bfloat16>(tmap, a, grid, smem, st);
-    return launch_one<MIX_DENSE, __half>(tmap, a, grid, smem, st);
+    if (mode == MIX_SPARSE)
+        return launch_dtype<MIX_SPARSE, kSparseR, kSparseWarps>(dtype, tmap, a, grid, smem, st);
+    return launch_dtype<MIX_DENSE, kDenseR, kDenseWarps>(dtype, tmap, a, grid, smem, st);
 }
 
 }  // namespace hrir

@@ -164,14 +164,15 @@ def hrir_render_batch(ctx, src, dirs, mode="sparse", full=True, length=None, out
     """src: CUDA [S][ld] float32/bfloat16/float16; dirs: CUDA int32 [S].
     Returns out: CUDA float32 [2][out_len] (or the given buffer)."""
     import torch
-    assert src.is_cuda and src.dim() == 2 and src.stride(1) == 1
-    S, ld = src.shape[0], src.stride(0) if src.shape[0] > 1 else src.shape[1]
+    assert src.is_cuda and src.dim() == 2 and (src.numel() == 0 or src.stride(1) == 1)
+    S = src.shape[0]
+    ld = src.stride(0) if S > 1 else src.shape[1]
     L = src.shape[1] if length is None else int(length)
     out_len = hrir_out_len(ctx, L, full)
     if out is None:
         out = torch.empty((2, max(out_len, 1)), dtype=torch.float32, device=src.device)
     assert out.is_cuda and out.dtype == torch.float32 and out.stride(1) == 1
-    assert dirs.is_cuda and dirs.dtype == torch.int32 and dirs.is_contiguous()
+    assert dirs.is_cuda and dirs.dtype == torch.int32 and (dirs.numel() == 0 or dirs.is_contiguous())
     rc = load_library().hrir_render_batch(
         ctx, S, L, ld, _dtype_code(src), src.data_ptr(), dirs.data_ptr(),
         MODES[mode] if isinstance(mode, str) else int(mode), int(full), out.data_ptr(),
@@ -185,7 +186,7 @@ def hrir_render_batch_host(ctx, src, dirs, mode="sparse", full=True, length=None
     """src: CPU tensor [S][ld] (pinned for speed); dirs: CPU int32 [S].  Synchronous; returns
     a CPU float32 [2][out_len] tensor."""
     import torch
-    assert (not src.is_cuda) and src.dim() == 2 and src.stride(1) == 1
+    assert (not src.is_cuda) and src.dim() == 2 and (src.numel() == 0 or src.stride(1) == 1)
     S = src.shape[0]
     ld = src.stride(0) if S > 1 else src.shape[1]
     L = src.shape[1] if length is None else int(length)
