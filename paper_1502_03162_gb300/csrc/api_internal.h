@@ -1,0 +1,90 @@
+// api_internal.h -- context structure and host helpers shared by the C-ABI translation
+// units (hrir_api.cu, noalloc.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdarg>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "../../include/hrir.h"
+#include "kernels.h"
+
+struct hrir_ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::string err;
+
+    bool loaded = false;
+    int n_dirs = 0, refl_len = 0, k_max = 0, res_len = 0, hrir_len = 0, fft_size = 0;
+    unsigned char *d_sparse = nullptr;  // (n_dirs + 1) sparse tap records
+    int sparse_rec_bytes = 0, sparse_nchunk = 0, sparse_nch_pad = 0;
+    float *d_dense = nullptr;           // (n_dirs + 1) x [2][dense_padded]
+    int dense_padded = 0, dense_nchunk = 0;
+    float *d_res = nullptr;             // [2][res_len]
+
+    float *d_partial = nullptr;
+    size_t partial_bytes = 0;
+    void *d_stage = nullptr;            // device staging for hrir_render_batch_host
+    size_t stage_bytes = 0;
+    int *d_status = nullptr;
+
+    // optional kernel timing (hrir_set_timing)
+    bool timing = false;
+    struct Pending {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> free_events;
+    double ms[HRIR_K_COUNT] = {};
+    int64_t launches[HRIR_K_COUNT] = {};
+};
+
+namespace hrir_host {
+
+// Record a failure message on ctx (or the thread's create-error slot) and return code.
+int fail(hrir_ctx *ctx, int code, const char *fmt, ...);
+size_t dtype_size(int dt);
+int64_t round_up(int64_t x, int64_t m);
+// Pipeline depth (2..4) that fits the 227 KB shared-memory limit; 0 if none does.
+int pick_stages(int buf_elems, int elem_bytes, int rec_bytes, size_t *smem);
+// 2-D tensor map over the sources: dims {len, n_src}, row stride ld, box {kMixBox, 1}.
+int make_source_map(hrir_ctx *ctx, CUtensorMap *m, const void *src, int dt, int64_t len,
+                    int64_t ld, int n_src);
+cudaEvent_t take_event(hrir_ctx *ctx);
+
+// Brackets one kernel launch with events when timing is enabled.
+struct KernelTimer {
+    hrir_ctx *ctx;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    KernelTimer(hrir_ctx *c, int k, cudaStream_t s) : ctx(c), kind(k), st(s)
+    {
+        if (ctx->timing) {
+            a = take_event(ctx);
+            cudaEventRecord(a, st);
+        }
+    }
+    void done()
+    {
+        if (!a) return;
+        cudaEvent_t b = take_event(ctx);
+        cudaEventRecord(b, st);
+        ctx->pending.push_back({kind, a, b});
+        a = nullptr;
+    }
+};
+
+}  // namespace hrir_host
+
+#define HRIR_CUDA_TRY(ctx, call)                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return hrir_host::fail((ctx), HRIR_ECUDA, "%s failed: %s", #call,             \
+                                   cudaGetErrorString(e_));                                \
+    } while (0)

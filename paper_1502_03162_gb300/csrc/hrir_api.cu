@@ -8,45 +8,11 @@
 #include <string>
 #include <vector>
 
-#include <cudaTypedefs.h>
-
-#include "../../include/hrir.h"
-#include "kernels.h"
+#include "api_internal.h"
 
 using namespace hrir;
 
-struct hrir_ctx {
-    int device = 0;
-    int num_sms = 0;
-    std::string err;
-
-    bool loaded = false;
-    int n_dirs = 0, refl_len = 0, k_max = 0, res_len = 0, hrir_len = 0, fft_size = 0;
-    unsigned char *d_sparse = nullptr;  // (n_dirs + 1) sparse tap records
-    int sparse_rec_bytes = 0, sparse_nchunk = 0, sparse_nch_pad = 0;
-    float *d_dense = nullptr;           // (n_dirs + 1) x [2][dense_padded]
-    int dense_padded = 0, dense_nchunk = 0;
-    float *d_res = nullptr;             // [2][res_len]
-
-    float *d_partial = nullptr;
-    size_t partial_bytes = 0;
-    void *d_stage = nullptr;            // device staging for hrir_render_batch_host
-    size_t stage_bytes = 0;
-    int *d_status = nullptr;
-
-    // optional kernel timing (hrir_set_timing)
-    bool timing = false;
-    struct Pending {
-        int kind;
-        cudaEvent_t a, b;
-    };
-    std::vector<Pending> pending;
-    std::vector<cudaEvent_t> free_events;
-    double ms[HRIR_K_COUNT] = {};
-    int64_t launches[HRIR_K_COUNT] = {};
-};
-
-namespace {
+namespace hrir_host {
 
 thread_local std::string g_create_err;
 
@@ -166,29 +132,6 @@ cudaEvent_t take_event(hrir_ctx *ctx)
     return e;
 }
 
-// Brackets one kernel launch with events when timing is enabled.
-struct KernelTimer {
-    hrir_ctx *ctx;
-    int kind;
-    cudaStream_t st;
-    cudaEvent_t a = nullptr;
-    KernelTimer(hrir_ctx *c, int k, cudaStream_t s) : ctx(c), kind(k), st(s)
-    {
-        if (ctx->timing) {
-            a = take_event(ctx);
-            cudaEventRecord(a, st);
-        }
-    }
-    void done()
-    {
-        if (!a) return;
-        cudaEvent_t b = take_event(ctx);
-        cudaEventRecord(b, st);
-        ctx->pending.push_back({kind, a, b});
-        a = nullptr;
-    }
-};
-
 void drop_timing_events(hrir_ctx *ctx)
 {
     for (auto &p : ctx->pending) {
@@ -200,7 +143,9 @@ void drop_timing_events(hrir_ctx *ctx)
     ctx->free_events.clear();
 }
 
-}  // namespace
+}  // namespace hrir_host
+
+using namespace hrir_host;
 
 extern "C" {
 
