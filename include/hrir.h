@@ -152,6 +152,30 @@ int hrir_render_batch_host(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld
                            int full, float *out, int64_t out_ld, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * hrir_render_batch_noalloc -- the same render as hrir_render_batch (HRIR_SPARSE or
+ * HRIR_DENSE, same arguments, same result), for callers that must not allocate device
+ * memory while rendering: real-time audio threads, where an allocator call can block for an
+ * unbounded time, and hosts that hand the library a fixed device-memory budget up front.
+ * The paper has no counterpart to this call; it exists only for those callers.
+ *
+ * hrir_render_batch keeps its partial sums in a workspace that it grows with cudaMalloc.
+ * This call uses instead a fixed 32 MiB array of device memory that every GPU loading the
+ * library holds until the process exits; it calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Renders whose partial sums need more than 32 MiB (about
+ * n_tiles * ceil(n_src / 64 + 2) * 80 KiB, n_tiles = ceil((len + Lg - 1) / 10240) for
+ * HRIR_SPARSE) are rejected with HRIR_EINVAL and a message giving the size needed.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.  Every call
+ * shares the one array, so calls whose GPU work overlaps in time (on different streams or
+ * from different contexts) race on it: serialize them.  Nothing in the array needs to be
+ * cleared between calls.
+ * ------------------------------------------------------------------------------------- */
+int hrir_render_batch_noalloc(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld,
+                              hrir_dtype dt, const void *src, const int32_t *dir,
+                              hrir_mode mode, int full, float *out, int64_t out_ld,
+                              void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * Optional kernel timing, for benchmarks.  While enabled, the library brackets each of its
  * kernel launches with CUDA events recorded on the launching stream.  hrir_kernel_times
  * waits for those events and writes, per kernel family (hrir_kernel), the accumulated

@@ -40,6 +40,7 @@ SIGNATURES = {
     "hrir_out_len": ([_vp, _i64, _i], _i64),
     "hrir_render_batch": ([_vp, _i, _i64, _i64, _i, _vp, _vp, _i, _i, _vp, _i64, _vp], _i),
     "hrir_render_batch_host": ([_vp, _i, _i64, _i64, _i, _vp, _vp, _i, _i, _vp, _i64, _vp], _i),
+    "hrir_render_batch_noalloc": ([_vp, _i, _i64, _i64, _i, _vp, _vp, _i, _i, _vp, _i64, _vp], _i),
     "hrir_set_timing": ([_vp, _i], _i),
     "hrir_kernel_times": ([_vp, _vp, _vp, _i], _i),
 }
@@ -196,6 +197,25 @@ def hrir_render_batch_host(ctx, src, dirs, mode="sparse", full=True, length=None
                           pin_memory=src.is_pinned())
     dirs = dirs.contiguous()
     rc = load_library().hrir_render_batch_host(
+        ctx, S, L, ld, _dtype_code(src), src.data_ptr(), dirs.data_ptr(),
+        MODES[mode] if isinstance(mode, str) else int(mode), int(full), out.data_ptr(),
+        out.stride(0), _stream_handle(stream))
+    _check(ctx, rc)
+    return out[:, :out_len]
+
+
+def hrir_render_batch_noalloc(ctx, src, dirs, out, mode="sparse", full=True, length=None,
+                              stream=None):
+    """The allocation-free variant of hrir_render_batch: the caller passes every buffer,
+    including `out` (CUDA float32 [2][>= out_len]); the library uses its fixed 32 MiB device
+    scratch array and allocates nothing.  Returns out[:, :out_len]."""
+    assert src.is_cuda and src.dim() == 2 and (src.numel() == 0 or src.stride(1) == 1)
+    S = src.shape[0]
+    ld = src.stride(0) if S > 1 else src.shape[1]
+    L = src.shape[1] if length is None else int(length)
+    out_len = hrir_out_len(ctx, L, full)
+    assert out.is_cuda and out.stride(1) == 1
+    rc = load_library().hrir_render_batch_noalloc(
         ctx, S, L, ld, _dtype_code(src), src.data_ptr(), dirs.data_ptr(),
         MODES[mode] if isinstance(mode, str) else int(mode), int(full), out.data_ptr(),
         out.stride(0), _stream_handle(stream))
