@@ -172,7 +172,9 @@ def run_reference(args):
     import oracle
     from paper_1502_03162_gb300 import synth
     oracle.build()
-    n_src = 16
+    # sources per step sized so that the whole run takes about 90 s of one core
+    # (about 0.045 s per source of 480000 samples)
+    n_src = int(max(1, min(16, round(90.0 / (0.045 * max(1, args.steps))))))
     cfg = synth.batched_config(S=n_src, L=L_DEFAULT, seed=2)
     idx, w, nnz = oracle.topk(cfg["G"], K_DEFAULT)
     for _ in range(args.warmup):

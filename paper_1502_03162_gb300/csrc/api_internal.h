@@ -24,6 +24,8 @@ struct hrir_ctx {
     float *d_dense = nullptr;           // (n_dirs + 1) x [2][dense_padded]
     int dense_padded = 0, dense_nchunk = 0;
     float *d_res = nullptr;             // [2][res_len]
+    float2 *d_tw = nullptr;             // FFT twiddles [kFftSize]
+    float2 *d_spec = nullptr;           // (n_dirs + 1) x [2][kFftBinsPadded] HRIR spectra
 
     float *d_partial = nullptr;
     size_t partial_bytes = 0;
@@ -53,7 +55,7 @@ int64_t round_up(int64_t x, int64_t m);
 int pick_stages(int buf_elems, int elem_bytes, int rec_bytes, size_t *smem);
 // 2-D tensor map over the sources: dims {len, n_src}, row stride ld, box {kMixBox, 1}.
 int make_source_map(hrir_ctx *ctx, CUtensorMap *m, const void *src, int dt, int64_t len,
-                    int64_t ld, int n_src);
+                    int64_t ld, int n_src, int box_rows = 1);
 cudaEvent_t take_event(hrir_ctx *ctx);
 
 // Brackets one kernel launch with events when timing is enabled.

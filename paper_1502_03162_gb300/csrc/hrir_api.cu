@@ -58,9 +58,13 @@ void free_tables(hrir_ctx *ctx)
     cudaFree(ctx->d_sparse);
     cudaFree(ctx->d_dense);
     cudaFree(ctx->d_res);
+    cudaFree(ctx->d_tw);
+    cudaFree(ctx->d_spec);
     ctx->d_sparse = nullptr;
     ctx->d_dense = nullptr;
     ctx->d_res = nullptr;
+    ctx->d_tw = nullptr;
+    ctx->d_spec = nullptr;
     ctx->loaded = false;
 }
 
@@ -102,7 +106,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 // 2-D tensor map over the sources: dims {len, n_src}, row stride ld elements, box
 // {kMixBox, 1}, out-of-range elements read as zero.
 int make_source_map(hrir_ctx *ctx, CUtensorMap *m, const void *src, int dt, int64_t len,
-                    int64_t ld, int n_src)
+                    int64_t ld, int n_src, int box_rows)
 {
     auto fn = tensor_map_encoder();
     if (!fn) return fail(ctx, HRIR_ECUDA, "cuTensorMapEncodeTiled is unavailable");
@@ -111,7 +115,7 @@ int make_source_map(hrir_ctx *ctx, CUtensorMap *m, const void *src, int dt, int6
                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const cuuint64_t dims[2] = {(cuuint64_t)len, (cuuint64_t)n_src};
     const cuuint64_t strides[1] = {(cuuint64_t)(ld * (int64_t)dtype_size(dt))};
-    const cuuint32_t box[2] = {(cuuint32_t)kMixBox, 1};
+    const cuuint32_t box[2] = {(cuuint32_t)kMixBox, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, ty, 2, const_cast<void *>(src), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -141,6 +145,66 @@ void drop_timing_events(hrir_ctx *ctx)
     ctx->pending.clear();
     for (auto e : ctx->free_events) cudaEventDestroy(e);
     ctx->free_events.clear();
+}
+
+// HRIR_FFT: overlap-save frames of P samples, hop B = P - G (G = H - 1 rounded up to 8).
+int render_fft(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hrir_dtype dt,
+               const void *src, const int32_t *dir, int64_t out_len, float *out, int64_t out_ld,
+               cudaStream_t st)
+{
+    const int guard = (int)round_up(ctx->hrir_len - 1, 8);
+    const int hop = kFftSize - guard;
+    const int64_t n_frames64 = (out_len + hop - 1) / hop;
+    if (n_frames64 > (1 << 30)) return fail(ctx, HRIR_EINVAL, "too many FFT frames");
+    const int n_frames = (int)n_frames64;
+    const int n_pairs = (n_src + 1) / 2;
+    Partition part;
+    part.U = (int64_t)n_frames * n_pairs;
+    part.P = std::min<int64_t>(ctx->num_sms, part.U);
+    part.n_src = n_pairs;
+    part.gs = kFftPairRun;
+    int slots = 0;
+    for (int f = 0; f < n_frames; ++f) slots = std::max(slots, part.slots(f));
+    const size_t pbytes = (size_t)n_frames * slots * 2 * kFftBinsPadded * sizeof(float2);
+    int rc = grow(ctx, (void **)&ctx->d_partial, &ctx->partial_bytes, pbytes);
+    if (rc) return rc;
+    CUtensorMap tmap;
+    rc = make_source_map(ctx, &tmap, src, (int)dt, len, src_ld, n_src, 2);
+    if (rc) return rc;
+    FftArgs a;
+    a.tw = ctx->d_tw;
+    a.spec = ctx->d_spec;
+    a.dir = dir;
+    a.n_src = n_src;
+    a.n_dirs = ctx->n_dirs;
+    a.hop = hop;
+    a.guard = guard;
+    a.part = part;
+    a.partial = reinterpret_cast<float2 *>(ctx->d_partial);
+    a.slots = slots;
+    a.status = ctx->d_status;
+    {
+        KernelTimer kt(ctx, HRIR_K_FFT, st);
+        HRIR_CUDA_TRY(ctx, launch_fft_mix((int)dt, tmap, a, (int)part.P,
+                                          fft_mix_smem_bytes((int)dtype_size(dt)), st));
+        kt.done();
+    }
+    FftOutArgs o;
+    o.partial = a.partial;
+    o.slots = slots;
+    o.part = part;
+    o.tw = ctx->d_tw;
+    o.hop = hop;
+    o.guard = guard;
+    o.out_len = out_len;
+    o.out = out;
+    o.out_ld = out_ld;
+    {
+        KernelTimer kt(ctx, HRIR_K_REDUCE, st);
+        HRIR_CUDA_TRY(ctx, launch_fft_out(o, n_frames, st));
+        kt.done();
+    }
+    return HRIR_OK;
 }
 
 }  // namespace hrir_host
@@ -266,10 +330,11 @@ int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k
     if (!tap_nnz || !resonance || (k_max > 0 && (!tap_idx || !tap_w)))
         return fail(ctx, HRIR_EINVAL, "NULL table pointer");
     const int hrir_len = res_len + refl_len - 1;
-    if (fft_size != 0 && (fft_size < 512 || fft_size > 8192 || (fft_size & (fft_size - 1)) ||
-                          fft_size <= hrir_len))
-        return fail(ctx, HRIR_EINVAL, "fft_size %d must be 0 or a power of two in [512, 8192] above H=%d",
-                    fft_size, hrir_len);
+    if (fft_size != 0 && fft_size != kFftSize)
+        return fail(ctx, HRIR_EINVAL, "fft_size %d: this build implements P = %d (pass 0 or %d)",
+                    fft_size, kFftSize, kFftSize);
+    if ((int)round_up(hrir_len - 1, 8) >= kFftSize)
+        return fail(ctx, HRIR_EINVAL, "HRIR length %d too long for the P = %d FFT frame", hrir_len, kFftSize);
     for (int64_t r = 0; r < (int64_t)n_dirs * 2; ++r) {
         const int k = tap_nnz[r];
         if (k > k_max) return fail(ctx, HRIR_EINVAL, "tap_nnz[%lld]=%d > k_max", (long long)r, k);
@@ -326,6 +391,24 @@ int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k
         if ((e = launch_build_dense_records(d_idx, d_w, d_nnz, n_dirs, (int)kk, ctx->d_res, res_len,
                                             hrir_len, dense_padded, ctx->d_dense, 0)) != cudaSuccess)
             break;
+        {
+            // FFT twiddles exp(-2 pi i k / P), computed in double on the host
+            std::vector<float2> tw(kFftSize);
+            for (int k = 0; k < kFftSize; ++k) {
+                const double ang = -2.0 * 3.14159265358979323846 * (double)k / (double)kFftSize;
+                tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+            }
+            if ((e = cudaMalloc(&ctx->d_tw, kFftSize * sizeof(float2))) != cudaSuccess) break;
+            if ((e = cudaMemcpy(ctx->d_tw, tw.data(), kFftSize * sizeof(float2),
+                                cudaMemcpyHostToDevice)) != cudaSuccess)
+                break;
+            if ((e = cudaMalloc(&ctx->d_spec, (size_t)(n_dirs + 1) * 2 * kFftBinsPadded *
+                                                  sizeof(float2))) != cudaSuccess)
+                break;
+            if ((e = launch_build_spectra(ctx->d_dense, dense_padded, hrir_len, n_dirs + 1, ctx->d_tw,
+                                          ctx->d_spec, 0)) != cudaSuccess)
+                break;
+        }
         e = cudaDeviceSynchronize();
     } while (0);
     cudaFree(d_idx);
@@ -384,9 +467,8 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
     if (src_ld < len || ((uintptr_t)src % 16) || ((src_ld * (int64_t)es) % 16))
         return fail(ctx, HRIR_EINVAL,
                     "src must be 16-byte aligned with src_ld >= len and src_ld*elem_size %% 16 == 0");
-    if (mode == HRIR_FFT) return fail(ctx, HRIR_EINVAL, "HRIR_FFT is not available in this build");
-
     if (len > (int64_t)1 << 31) return fail(ctx, HRIR_EINVAL, "len must be < 2^31");
+    if (mode == HRIR_FFT) return render_fft(ctx, n_src, len, src_ld, dt, src, dir, out_len, out, out_ld, st);
 
     const bool sparse = mode == HRIR_SPARSE;
     const int nchunk = sparse ? ctx->sparse_nchunk : ctx->dense_nchunk;

@@ -78,6 +78,45 @@ struct ReduceArgs {
 };
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
 
+// ---- overlap-save FFT convolution with frequency-domain mixing -------------------------
+constexpr int kFftSize = 4096;                    // frame P
+constexpr int kFftBinsPadded = kFftSize / 2 + 8;  // P/2 + 1 bins, row stride padded
+constexpr int kFftPairRun = 32;                   // source pairs per accumulation run
+
+struct FftArgs {
+    const float2 *tw;        // [P] exp(-2 pi i k / P)
+    const float2 *spec;      // [(n_dirs + 1)][2][kFftBinsPadded] HRIR spectra (last: silent)
+    const int32_t *dir;      // [n_src]
+    int n_src;
+    int n_dirs;
+    int hop;                 // B = P - guard outputs per frame
+    int guard;               // G = H - 1 rounded up to 8
+    Partition part;          // units = frames x source pairs (part.n_src = pairs)
+    float2 *partial;         // [n_frames][slots][2][kFftBinsPadded]
+    int slots;
+    int *status;
+};
+
+struct FftOutArgs {
+    const float2 *partial;
+    int slots;
+    Partition part;
+    const float2 *tw;
+    int hop;
+    int guard;
+    int64_t out_len;
+    float *out;
+    int64_t out_ld;
+};
+
+size_t fft_mix_smem_bytes(int elem_bytes);
+cudaError_t launch_build_spectra(const float *dense, int padded_len, int hrir_len, int n_records,
+                                 const float2 *tw, float2 *spec, cudaStream_t st);
+// tmap: 2-D tensor map over the sources with box {256, 2} (one source pair per box)
+cudaError_t launch_fft_mix(int dtype, const CUtensorMap &tmap, const FftArgs &a, int grid,
+                           size_t smem, cudaStream_t st);
+cudaError_t launch_fft_out(const FftOutArgs &a, int n_frames, cudaStream_t st);
+
 // ---- table builders and top-K -------------------------------------------------------------
 cudaError_t launch_topk(const float *g, int n_rows, int refl_len, int k, uint16_t *idx, float *w,
                         uint8_t *nnz, cudaStream_t st);

@@ -49,7 +49,10 @@ def test_topk_pack_bit_exact(rend, refl_len):
 
 
 # ------------------------------------------------------------------------------ rendering
-def _render_both(rend, y, dirs, idx, w, nnz, res, modes=("sparse", "dense"), length=None,
+MODES = ("sparse", "dense", "fft")
+
+
+def _render_both(rend, y, dirs, idx, w, nnz, res, modes=MODES, length=None,
                  dtype=None, refl_len=200):
     rend.load_filters(idx, w, nnz, refl_len, res)
     yd = _dev(y, dtype)
@@ -70,7 +73,7 @@ def test_tiny_config_matches_oracle(rend):
     ref = oracle.render_sparse(cfg["y"], cfg["dirs"], idx, w, nnz, 200, cfg["res"])
     outs = _render_both(rend, cfg["y"], cfg["dirs"], idx, w, nnz, cfg["res"])
     L = cfg["y"].shape[1]
-    for m in ("sparse", "dense"):
+    for m in MODES:
         assert outs[(m, True)].shape == (2, L + 230)
         assert_close(outs[(m, True)], ref, what=f"tiny {m} full")
         assert outs[(m, False)].shape == (2, L)
@@ -88,7 +91,7 @@ def test_batched_matches_oracle(rend, S, L, k, n_dirs):
     dirs = synth.directions(rng, S, n_dirs)
     ref = oracle.render_sparse(y, dirs, idx, w, nnz, 200, res, length=L)
     outs = _render_both(rend, y, dirs, idx, w, nnz, res, length=L)
-    for m in ("sparse", "dense"):
+    for m in MODES:
         assert np.isfinite(outs[(m, True)]).all()
         assert_close(outs[(m, True)], ref, what=f"{m} S={S} L={L}")
         assert_close(outs[(m, False)], ref[:, :L], what=f"{m} same S={S} L={L}")
@@ -104,14 +107,15 @@ def test_edge_cases(rend):
         y = rng.standard_normal((6, (L + 7) // 8 * 8)).astype(np.float32)
         dirs = np.array([0, 1, 2, 3, 0, 3], np.int32)
         ref = oracle.render_sparse(y, dirs, idx, w, nnz, 200, res, length=L)
-        for m in ("sparse", "dense"):
+        for m in MODES:
             o = rend.render(_dev(y), _dev(dirs), mode=m, length=L).cpu().numpy()
             assert rend.sync() == 0
             assert_close(o, ref, what=f"{m} L={L}")
     # silent direction only -> exact zeros
     y = rng.standard_normal((2, 64)).astype(np.float32)
-    o = rend.render(_dev(y), _dev(np.array([3, 3], np.int32))).cpu().numpy()
-    assert not o.any()
+    for m in MODES:
+        o = rend.render(_dev(y), _dev(np.array([3, 3], np.int32)), mode=m).cpu().numpy()
+        assert not o.any()
     # no sources -> zeros of full length; empty sources -> empty output
     o = rend.render(_dev(np.zeros((0, 64), np.float32)), _dev(np.zeros(0, np.int32)), length=64)
     assert o.shape == (2, 64 + 230) and not o.cpu().numpy().any()
@@ -125,11 +129,12 @@ def test_bad_direction_is_silent_and_flagged(rend):
     _, idx, w, nnz, res = tables(rng, 4, 16)
     rend.load_filters(idx, w, nnz, 200, res)
     y = rng.standard_normal((3, 1000)).astype(np.float32)
-    o = rend.render(_dev(y), _dev(np.array([1, 9, -2], np.int32))).cpu().numpy()
-    assert rend.sync() == hrir.HRIR_EINVAL
-    assert rend.sync() == 0                              # flag cleared
     ref = oracle.render_sparse(y[:1], np.array([1], np.int32), idx, w, nnz, 200, res)
-    assert_close(o, ref, what="bad dirs")
+    for m in MODES:
+        o = rend.render(_dev(y), _dev(np.array([1, 9, -2], np.int32)), mode=m).cpu().numpy()
+        assert rend.sync() == hrir.HRIR_EINVAL
+        assert rend.sync() == 0                          # flag cleared
+        assert_close(o, ref, what=f"bad dirs {m}")
 
 
 def test_invalid_arguments_rejected(rend):
@@ -164,7 +169,7 @@ def test_16bit_sources(rend, dt):
     dirs = synth.directions(rng, S, 40)
     ref = oracle.render_sparse(ydq, dirs, idx, w, nnz, 200, res, length=L)
     rend.load_filters(idx, w, nnz, 200, res)
-    for m in ("sparse", "dense"):
+    for m in MODES:
         o = rend.render(yq.cuda(), _dev(dirs), mode=m, length=L).cpu().numpy()
         assert rend.sync() == 0
         assert_close(o, ref, what=f"{dt} {m}")
@@ -204,8 +209,9 @@ def test_full_size_batched_config_sampled(rend, k):
     y = cfg["y"]
     L = y.shape[1]
     out = {}
-    for m in ("sparse", "dense"):
-        o = rend.render(torch.from_numpy(y).cuda(), _dev(cfg["dirs"]), mode=m)
+    yd = torch.from_numpy(y).cuda()
+    for m in MODES:
+        o = rend.render(yd, _dev(cfg["dirs"]), mode=m)
         assert rend.sync() == 0
         out[m] = o.cpu().numpy()
         assert out[m].shape == (2, L + 230) and np.isfinite(out[m]).all()
@@ -214,7 +220,7 @@ def test_full_size_batched_config_sampled(rend, k):
                                     rng.integers(0, L + 230, 40)]))
     ref = oracle.render_at(y, cfg["dirs"], idx, w, nnz, 200, cfg["res"], pos)
     # tolerance scale: RMS of the whole GPU output (the oracle has only samples)
-    for m in ("sparse", "dense"):
+    for m in MODES:
         rms = np.sqrt(np.mean(out[m].astype(np.float64) ** 2, axis=1))
         err = np.max(np.abs(out[m][:, pos] - ref), axis=1)
         assert np.all(err <= TOL * rms), f"{m} K={k}: err {err} rms {rms}"
