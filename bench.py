@@ -6,8 +6,8 @@ non-negative reflection taps of 200 per (direction, ear), 32-tap resonance per e
 the full-length stereo mix.  One step = one hrir_render_batch call (sparse gather-FMA mix
 kernel + fixed-order reduction/resonance kernel) over the whole batch, inputs resident in
 HBM (1.97 GB, larger than the 129 MB L2, so no flush is needed).  The same batch is also
-rendered by the dense-HRIR direct path and with K = 8 and K = 32; those numbers are extra
-keys of the same JSON line.
+rendered by the dense-HRIR direct path, by overlap-save FFT convolution (P = 4096), and with
+K = 8 and K = 32; those numbers are extra keys ("paths") of the same JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -318,6 +318,11 @@ def main():
                        max(2, args.steps // 5), 1, torch, barrier)
         t = max_over_ranks(t)
         extras["dense_k16"] = {"value": units * world / (t / 1e3), "ms_per_step": t}
+        # overlap-save FFT convolution (plain method 2), same filters, P = 4096
+        t = time_steps(lambda: rend.render(src, dirs, mode="fft", length=L, out=out),
+                       max(3, args.steps // 5), 2, torch, barrier)
+        t = max_over_ranks(t)
+        extras["fft_p4096"] = {"value": units * world / (t / 1e3), "ms_per_step": t}
         for k in (8, 32):
             load(k)
             t = time_steps(step, max(3, args.steps // 2), 2, torch, barrier)

@@ -152,6 +152,40 @@ int hrir_render_batch_host(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld
                            int full, float *out, int64_t out_ld, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Block streaming with continuous batching: partitioned time-domain convolution, which
+ * "incurs neither memory overhead nor latency" (Sec. IV-G), on the filters of Eqs. 1-2.
+ *
+ * hrir_stream_open  Opens the context's stream: blocks of `block` (128 or 256) samples, at most
+ *                   max_slots sources at once, a device pool of pool_bytes for source samples;
+ *                   steps run on `stream`.  Captures the step as a CUDA graph.  Closes any
+ *                   previous stream; hrir_load_filters also closes it.
+ * hrir_stream_admit Admits one source (HOST samples [len], FP32; page-locked memory uploads
+ *                   fastest) into session `session` at direction dir.  Returns HRIR_EBUSY when
+ *                   no slot is free and HRIR_ENOMEM when the pool has no room: the request was
+ *                   not admitted and may be retried after later steps free resources.  The
+ *                   upload runs on a copy stream, overlapping earlier steps; the source joins
+ *                   the next step (which waits for the upload on the GPU), starting at that
+ *                   step's block.  host_src must stay valid until that step has returned.
+ *                   Sources of one session are mixed into one stereo stream.
+ * hrir_stream_step  Renders one block for every session that has a ready source and waits for
+ *                   it.  *out_blocks points to n_out blocks [n_out][2][block] (FP32, row r
+ *                   belongs to session (*out_sessions)[r]); both arrays stay valid until the
+ *                   next step.  done_ids (capacity max_slots, may be NULL) receives the ids of
+ *                   the *n_done requests that finished in this step: a source finishes after
+ *                   len + H - 1 samples (its full convolution) have been emitted.
+ * hrir_stream_stats Active (rendering) and pending (admitted, not yet stepped) sources and pool
+ *                   bytes in use.
+ * hrir_stream_close Releases the stream (waits for its work).
+ * ------------------------------------------------------------------------------------- */
+int hrir_stream_open(hrir_ctx *ctx, int block, int max_slots, size_t pool_bytes, void *stream);
+int hrir_stream_admit(hrir_ctx *ctx, int64_t req_id, int64_t session, const float *host_src,
+                      int64_t len, int dir);
+int hrir_stream_step(hrir_ctx *ctx, const float **out_blocks, const int64_t **out_sessions,
+                     int *n_out, int64_t *done_ids, int *n_done);
+int hrir_stream_stats(hrir_ctx *ctx, int *active, int *pending, int64_t *pool_used_bytes);
+int hrir_stream_close(hrir_ctx *ctx);
+
+/* ---------------------------------------------------------------------------------------
  * hrir_render_batch_noalloc -- the same render as hrir_render_batch (HRIR_SPARSE or
  * HRIR_DENSE, same arguments, same result), for callers that must not allocate device
  * memory while rendering: real-time audio threads, where an allocator call can block for an

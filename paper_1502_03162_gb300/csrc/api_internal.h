@@ -12,6 +12,8 @@
 #include "../../include/hrir.h"
 #include "kernels.h"
 
+struct hrir_stream;  // streaming state (stream.cu)
+
 struct hrir_ctx {
     int device = 0;
     int num_sms = 0;
@@ -24,6 +26,10 @@ struct hrir_ctx {
     float *d_dense = nullptr;           // (n_dirs + 1) x [2][dense_padded]
     int dense_padded = 0, dense_nchunk = 0;
     float *d_res = nullptr;             // [2][res_len]
+    uint16_t *d_tap_idx = nullptr;      // [n_dirs][2][k_max] (streaming kernel)
+    float *d_tap_w = nullptr;
+    uint8_t *d_tap_nnz = nullptr;
+    hrir_stream *stream = nullptr;      // open block stream, if any
     float2 *d_tw = nullptr;             // FFT twiddles [kFftSize]
     float2 *d_spec = nullptr;           // (n_dirs + 1) x [2][kFftBinsPadded] HRIR spectra
 

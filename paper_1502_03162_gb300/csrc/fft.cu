@@ -140,7 +140,7 @@ __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v)
 // Shared memory: two TMA stages of [kN/256 boxes][2 rows][256] source samples, the padded
 // FFT buffer, two mbarriers.
 template <typename T>
-__global__ void __launch_bounds__(kT, 1)
+__global__ void __launch_bounds__(kT, kFftCtasPerSm)
     fft_mix_kernel(const __grid_constant__ CUtensorMap tmap, const FftArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];

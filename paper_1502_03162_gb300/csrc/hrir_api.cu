@@ -60,6 +60,12 @@ void free_tables(hrir_ctx *ctx)
     cudaFree(ctx->d_res);
     cudaFree(ctx->d_tw);
     cudaFree(ctx->d_spec);
+    cudaFree(ctx->d_tap_idx);
+    cudaFree(ctx->d_tap_w);
+    cudaFree(ctx->d_tap_nnz);
+    ctx->d_tap_idx = nullptr;
+    ctx->d_tap_w = nullptr;
+    ctx->d_tap_nnz = nullptr;
     ctx->d_sparse = nullptr;
     ctx->d_dense = nullptr;
     ctx->d_res = nullptr;
@@ -160,7 +166,7 @@ int render_fft(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hrir_dtype
     const int n_pairs = (n_src + 1) / 2;
     Partition part;
     part.U = (int64_t)n_frames * n_pairs;
-    part.P = std::min<int64_t>(ctx->num_sms, part.U);
+    part.P = std::min<int64_t>((int64_t)ctx->num_sms * kFftCtasPerSm, part.U);
     part.n_src = n_pairs;
     part.gs = kFftPairRun;
     int slots = 0;
@@ -244,6 +250,7 @@ void hrir_destroy(hrir_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    hrir_stream_close(ctx);
     free_tables(ctx);
     drop_timing_events(ctx);
     cudaFree(ctx->d_partial);
@@ -354,6 +361,7 @@ int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k
 
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     CUDA_TRY(ctx, cudaDeviceSynchronize());
+    hrir_stream_close(ctx);  // a stream's graph refers to the old tables
     free_tables(ctx);
 
     const size_t rows = (size_t)n_dirs * 2;
@@ -411,16 +419,19 @@ int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k
         }
         e = cudaDeviceSynchronize();
     } while (0);
-    cudaFree(d_idx);
-    cudaFree(d_w);
-    cudaFree(d_nnz);
     if (e != cudaSuccess) {
+        cudaFree(d_idx);
+        cudaFree(d_w);
+        cudaFree(d_nnz);
         free_tables(ctx);
         rc = fail(ctx, e == cudaErrorMemoryAllocation ? HRIR_ENOMEM : HRIR_ECUDA,
                   "filter table construction failed: %s", cudaGetErrorString(e));
         cudaGetLastError();
         return rc;
     }
+    ctx->d_tap_idx = d_idx;  // kept for the streaming kernel
+    ctx->d_tap_w = d_w;
+    ctx->d_tap_nnz = d_nnz;
     ctx->n_dirs = n_dirs;
     ctx->refl_len = refl_len;
     ctx->k_max = k_max;

@@ -82,6 +82,7 @@ cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
 constexpr int kFftSize = 4096;                    // frame P
 constexpr int kFftBinsPadded = kFftSize / 2 + 8;  // P/2 + 1 bins, row stride padded
 constexpr int kFftPairRun = 32;                   // source pairs per accumulation run
+constexpr int kFftCtasPerSm = 2;                  // two 512-thread CTAs overlap their phases
 
 struct FftArgs {
     const float2 *tw;        // [P] exp(-2 pi i k / P)

@@ -41,6 +41,14 @@ SIGNATURES = {
     "hrir_render_batch": ([_vp, _i, _i64, _i64, _i, _vp, _vp, _i, _i, _vp, _i64, _vp], _i),
     "hrir_render_batch_host": ([_vp, _i, _i64, _i64, _i, _vp, _vp, _i, _i, _vp, _i64, _vp], _i),
     "hrir_render_batch_noalloc": ([_vp, _i, _i64, _i64, _i, _vp, _vp, _i, _i, _vp, _i64, _vp], _i),
+    "hrir_stream_open": ([_vp, _i, _i, ctypes.c_size_t, _vp], _i),
+    "hrir_stream_admit": ([_vp, _i64, _i64, _vp, _i64, _i], _i),
+    "hrir_stream_step": ([_vp, ctypes.POINTER(ctypes.POINTER(ctypes.c_float)),
+                          ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)),
+                          ctypes.POINTER(ctypes.c_int), _vp, ctypes.POINTER(ctypes.c_int)], _i),
+    "hrir_stream_stats": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_int64)], _i),
+    "hrir_stream_close": ([_vp], _i),
     "hrir_set_timing": ([_vp, _i], _i),
     "hrir_kernel_times": ([_vp, _vp, _vp, _i], _i),
 }
@@ -221,6 +229,89 @@ def hrir_render_batch_noalloc(ctx, src, dirs, out, mode="sparse", full=True, len
         out.stride(0), _stream_handle(stream))
     _check(ctx, rc)
     return out[:, :out_len]
+
+
+def hrir_stream_open(ctx, block: int, max_slots: int, pool_bytes: int, stream=None) -> None:
+    _check(ctx, load_library().hrir_stream_open(ctx, block, max_slots, pool_bytes,
+                                                _stream_handle(stream)))
+
+
+def hrir_stream_admit(ctx, req_id: int, session: int, src, direction: int) -> int:
+    """src: host float32 samples (numpy array or CPU tensor; must stay alive until the
+    source's upload has landed -- page-locked buffers are read asynchronously).  Returns the
+    status: HRIR_OK, or HRIR_EBUSY / HRIR_ENOMEM when the request was not admitted now.
+    Other errors raise."""
+    if hasattr(src, "data_ptr"):
+        assert src.dtype.__str__() == "torch.float32" and src.is_contiguous() and not src.is_cuda
+        ptr, n = src.data_ptr(), src.numel()
+    else:
+        assert src.dtype == np.float32 and src.flags.c_contiguous
+        ptr, n = src.ctypes.data, src.size
+    rc = load_library().hrir_stream_admit(ctx, int(req_id), int(session), ptr, int(n),
+                                          int(direction))
+    if rc not in (HRIR_OK, HRIR_EBUSY, HRIR_ENOMEM):
+        _check(ctx, rc)
+    return rc
+
+
+class _StepBuffers:
+    def __init__(self, max_slots):
+        self.done = (ctypes.c_int64 * max_slots)()
+        self.out = ctypes.POINTER(ctypes.c_float)()
+        self.sess = ctypes.POINTER(ctypes.c_int64)()
+        self.n_out = ctypes.c_int()
+        self.n_done = ctypes.c_int()
+
+
+def hrir_stream_step(ctx, bufs: "_StepBuffers", block: int):
+    """One step.  Returns (blocks, sessions, done): blocks is a float32 view [n][2][block] of
+    the library's output buffer (valid until the next step), sessions and done are lists."""
+    lib = load_library()
+    rc = lib.hrir_stream_step(ctx, ctypes.byref(bufs.out), ctypes.byref(bufs.sess),
+                              ctypes.byref(bufs.n_out), bufs.done, ctypes.byref(bufs.n_done))
+    _check(ctx, rc)
+    n = bufs.n_out.value
+    if n:
+        blocks = np.ctypeslib.as_array(bufs.out, shape=(n, 2, block))
+        sessions = np.ctypeslib.as_array(bufs.sess, shape=(n,)).tolist()
+    else:
+        blocks, sessions = np.zeros((0, 2, block), np.float32), []
+    return blocks, sessions, list(bufs.done[:bufs.n_done.value])
+
+
+def hrir_stream_stats(ctx):
+    a, p, u = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    _check(ctx, load_library().hrir_stream_stats(ctx, ctypes.byref(a), ctypes.byref(p),
+                                                 ctypes.byref(u)))
+    return a.value, p.value, u.value
+
+
+def hrir_stream_close(ctx) -> None:
+    _check(ctx, load_library().hrir_stream_close(ctx))
+
+
+class Stream:
+    """Block stream on a Renderer (continuous batching of sources into sessions)."""
+
+    def __init__(self, renderer: "Renderer", block: int, max_slots: int, pool_bytes: int,
+                 stream=None):
+        self.r = renderer
+        self.block = block
+        self.max_slots = max_slots
+        hrir_stream_open(renderer.ctx, block, max_slots, pool_bytes, stream)
+        self.bufs = _StepBuffers(max_slots)
+
+    def admit(self, req_id, session, src, direction) -> int:
+        return hrir_stream_admit(self.r.ctx, req_id, session, src, direction)
+
+    def step(self):
+        return hrir_stream_step(self.r.ctx, self.bufs, self.block)
+
+    def stats(self):
+        return hrir_stream_stats(self.r.ctx)
+
+    def close(self):
+        hrir_stream_close(self.r.ctx)
 
 
 def hrir_set_timing(ctx, enable: bool) -> None:
