@@ -196,6 +196,63 @@ def run_reference(args):
                 "d2h_bytes_per_step": 0}}))
 
 
+def bench_stream(rend, torch, block, warm_audio_s=10.0, audio_s=60.0, seed=12, rate=200.0,
+                 fs=48000, max_slots=8192, pool_bytes=768 << 20):
+    """Serving loop: Poisson arrivals (rate per second of audio), source lengths log-uniform in
+    [0.1, 30] s, one session per source, admission bound by slots and the device pool.  The
+    arrival clock is audio time (unpaced).  Returns latency percentiles of hrir_stream_step
+    and throughput in source-ear samples per wall second."""
+    from paper_1502_03162_gb300 import hrir
+    rng = np.random.default_rng(seed)
+    noise = torch.empty(1 << 25, dtype=torch.float32, pin_memory=True)   # 128 MB of sources
+    noise.numpy()[:] = rng.standard_normal(noise.numel(), dtype=np.float32)
+    nz = noise.numpy()
+    st = hrir.Stream(rend, block, max_slots, pool_bytes)
+    n_dirs = 1250
+    t_audio, next_arrival, req = 0.0, rng.exponential(1.0 / rate), 0
+    queue = []
+    lat, rows_hist, refused = [], [], 0
+    samples = 0
+    total_steps = int((warm_audio_s + audio_s) * fs / block)
+    warm_steps = int(warm_audio_s * fs / block)
+    t_wall0 = None
+    for step in range(total_steps):
+        t_audio += block / fs
+        while next_arrival <= t_audio:
+            n = int(round(np.exp(rng.uniform(np.log(0.1), np.log(30.0))) * fs))
+            off = int(rng.integers(0, nz.size - n))
+            queue.append((req, nz[off:off + n], int(rng.integers(0, n_dirs))))
+            req += 1
+            next_arrival += rng.exponential(1.0 / rate)
+        while queue:
+            rid, y, d = queue[0]
+            rc = st.admit(rid, rid, y, d)
+            if rc != hrir.HRIR_OK:
+                refused += 1
+                break
+            queue.pop(0)
+        if step == warm_steps:
+            torch.cuda.synchronize()
+            t_wall0 = time.perf_counter()
+        t0 = time.perf_counter()
+        blocks, sessions, done = st.step()
+        t1 = time.perf_counter()
+        if step >= warm_steps:
+            lat.append(t1 - t0)
+            rows_hist.append(len(sessions))
+            samples += len(sessions) * block * 2
+    wall = time.perf_counter() - t_wall0
+    st.close()
+    lat_ms = np.array(lat) * 1e3
+    return {"block": block, "p50_ms": float(np.percentile(lat_ms, 50)),
+            "p99_ms": float(np.percentile(lat_ms, 99)), "max_ms": float(lat_ms.max()),
+            "value": samples / wall, "unit": "source-ear samples/s",
+            "mean_active_sources": float(np.mean(rows_hist)), "max_active_sources": int(max(rows_hist)),
+            "steps": len(lat), "audio_s": audio_s, "realtime_factor": audio_s / wall,
+            "refused_admissions": refused, "pool_bytes": pool_bytes, "max_slots": max_slots,
+            "arrivals_per_s": rate}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -206,6 +263,7 @@ def main():
     ap.add_argument("--length", type=int, default=L_DEFAULT)
     ap.add_argument("--no-extras", action="store_true", help="only the headline sparse K=16 path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stream", action="store_true", help="skip the serving-loop benchmark")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -346,6 +404,11 @@ def main():
     result["e2e"] = {"value": units * world / (e2e_ms / 1e3), "unit": "source-ear samples/s",
                      "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(S * host.shape[1] * 4 + S * 4),
                      "d2h_bytes_per_step": int(2 * (L + 230) * 4)}
+
+    if not args.no_stream:
+        load(K_DEFAULT)
+        result["stream"] = {f"B{b}": bench_stream(rend, torch, b) for b in (256, 128)}
+        result["p99_block_latency_ms"] = {k: v["p99_ms"] for k, v in result["stream"].items()}
 
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(cfg, *tables16, cfg["res"])

@@ -67,7 +67,10 @@ def test_single_source_stream_equals_full_convolution(rend, block):
     ref = oracle.render_sparse(y[None], np.array([5], np.int32), idx, w, nnz, 200, res)
     assert_close(z[:, :n_full], ref, what=f"stream B={block}")
     assert not z[:, n_full:].any()
-    b = rend.render(torch.from_numpy(y[None].copy()).cuda(), torch.tensor([5], dtype=torch.int32, device="cuda"))
+    yp = np.zeros((1, (L + 7) // 8 * 8), np.float32)
+    yp[0, :L] = y
+    b = rend.render(torch.from_numpy(yp).cuda(), torch.tensor([5], dtype=torch.int32, device="cuda"),
+                    length=L)
     assert_close(z[:, :n_full], b.cpu().numpy(), what="stream vs batch")
 
 
