@@ -197,7 +197,7 @@ def run_reference(args):
 
 
 def bench_stream(rend, torch, block, warm_audio_s=10.0, audio_s=60.0, seed=12, rate=200.0,
-                 fs=48000, max_slots=8192, pool_bytes=768 << 20):
+                 fs=48000, max_slots=8192, pool_bytes=4 << 30):
     """Serving loop: Poisson arrivals (rate per second of audio), source lengths log-uniform in
     [0.1, 30] s, one session per source, admission bound by slots and the device pool.  The
     arrival clock is audio time (unpaced).  Returns latency percentiles of hrir_stream_step

@@ -22,7 +22,9 @@ struct hrir_ctx {
     bool loaded = false;
     int n_dirs = 0, refl_len = 0, k_max = 0, res_len = 0, hrir_len = 0, fft_size = 0;
     unsigned char *d_sparse = nullptr;  // (n_dirs + 1) sparse tap records
-    int sparse_rec_bytes = 0, sparse_nchunk = 0, sparse_nch_pad = 0;
+    int sparse_rec_bytes = 0;
+    int sparse_nchunk = 0;   // window segments of kSparseSegment filter offsets
+    int sparse_nch_pad = 0;  // segment-count array length in a record (even)
     float *d_dense = nullptr;           // (n_dirs + 1) x [2][dense_padded]
     int dense_padded = 0, dense_nchunk = 0;
     float *d_res = nullptr;             // [2][res_len]

@@ -369,9 +369,9 @@ int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k
     uint16_t *d_idx = nullptr;
     float *d_w = nullptr;
     uint8_t *d_nnz = nullptr;
-    const int sparse_nchunk = (refl_len + kSparseR - 1) / kSparseR;
-    const int sparse_nch_pad = (int)round_up(sparse_nchunk, 8);
-    const int sparse_rec = (int)round_up(16 + 2 * sparse_nch_pad + 2 * (int64_t)k_max * 8, 16);
+    const int sparse_nseg = (refl_len + kSparseSegment - 1) / kSparseSegment;
+    const int sparse_nseg_pad = (int)round_up(sparse_nseg, 2);
+    const int sparse_rec = (int)round_up(16 + 8 * sparse_nseg_pad + 2 * (int64_t)k_max * 8, 16);
     const int dense_nchunk = (hrir_len + kDenseR - 1) / kDenseR;
     const int dense_padded = dense_nchunk * kDenseR;
     int rc = HRIR_OK;
@@ -392,9 +392,9 @@ int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k
         if ((e = cudaMemcpy(ctx->d_res, resonance, 2 * (size_t)res_len * 4, cudaMemcpyHostToDevice)) !=
             cudaSuccess)
             break;
-        if ((e = launch_build_sparse_records(d_idx, d_w, d_nnz, n_dirs, (int)kk, kSparseR,
-                                             sparse_nch_pad, ctx->d_sparse, sparse_rec, 0)) !=
-            cudaSuccess)
+        if ((e = launch_build_sparse_records(d_idx, d_w, d_nnz, n_dirs, (int)kk, kSparseSegment,
+                                             sparse_nseg, sparse_nseg_pad, ctx->d_sparse, sparse_rec,
+                                             0)) != cudaSuccess)
             break;
         if ((e = launch_build_dense_records(d_idx, d_w, d_nnz, n_dirs, (int)kk, ctx->d_res, res_len,
                                             hrir_len, dense_padded, ctx->d_dense, 0)) != cudaSuccess)
@@ -439,8 +439,8 @@ int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k
     ctx->hrir_len = hrir_len;
     ctx->fft_size = fft_size;
     ctx->sparse_rec_bytes = sparse_rec;
-    ctx->sparse_nchunk = sparse_nchunk;
-    ctx->sparse_nch_pad = sparse_nch_pad;
+    ctx->sparse_nchunk = sparse_nseg;
+    ctx->sparse_nch_pad = sparse_nseg_pad;
     ctx->dense_nchunk = dense_nchunk;
     ctx->dense_padded = dense_padded;
     ctx->loaded = true;
@@ -485,7 +485,7 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
     const int nchunk = sparse ? ctx->sparse_nchunk : ctx->dense_nchunk;
     const MixShape shape = mix_shape(sparse ? MIX_SPARSE : MIX_DENSE);
     const int tile = shape.tile;
-    const int halo = (int)round_up((int64_t)nchunk * shape.r, 8);
+    const int halo = (int)round_up((int64_t)nchunk * (sparse ? kSparseSegment : shape.r), 8);
     const int buf_elems = (int)round_up(halo + tile, kMixBox);
     const int rec_bytes = sparse ? ctx->sparse_rec_bytes : 2 * ctx->dense_padded * 4;
     const int64_t mix_len = sparse ? std::min<int64_t>(out_len, len + ctx->refl_len - 1) : out_len;

@@ -12,19 +12,18 @@ namespace hrir {
 // ---- direct-convolution mixing (sparse reflection taps, or dense HRIR) -----------------
 // Outputs per lane (= window chunk width) and warps per CTA of each mixing kernel.  All warps
 // compute; warp 0 also issues the TMA loads.  The tile is warps x 32 lanes x R outputs.
-#ifndef HRIR_SPARSE_R
-#define HRIR_SPARSE_R 20
-#endif
-#ifndef HRIR_SPARSE_WARPS
-#define HRIR_SPARSE_WARPS 16
-#endif
 #ifndef HRIR_DENSE_R
 #define HRIR_DENSE_R 36
 #endif
 #ifndef HRIR_DENSE_WARPS
 #define HRIR_DENSE_WARPS 8
 #endif
-constexpr int kSparseR = HRIR_SPARSE_R, kSparseWarps = HRIR_SPARSE_WARPS;
+// Sparse kernel: windows in tensor memory, 8 warps x 32 lanes x 36 outputs (tile 9216); a
+// warp's TMEM row holds kSparseTmemCols samples = one segment of kSparseSegment filter
+// offsets plus the lane's outputs.
+constexpr int kSparseR = 36, kSparseWarps = 8;
+constexpr int kSparseTmemCols = 256;
+constexpr int kSparseSegment = kSparseTmemCols - kSparseR;  // 220
 constexpr int kDenseR = HRIR_DENSE_R, kDenseWarps = HRIR_DENSE_WARPS;
 constexpr int kMixMaxR = 36;
 constexpr int kMixMaxStages = 4;
@@ -42,8 +41,8 @@ struct MixArgs {
     int n_dirs;
     const unsigned char *table; // per-direction records (n_dirs + 1, last one silent)
     int rec_bytes;              // record stride, multiple of 16
-    int nchunk;                 // filter span in window chunks of R (sparse: per-chunk
-                                // count array length, padded to a multiple of 8)
+    int nchunk;                 // dense: filter span in chunks of R; sparse: length of the
+                                // per-segment count array of a record (even)
     int halo;                   // >= nchunk * R samples of history per tile (multiple of 8)
     int buf_elems;              // per-stage source buffer, multiple of kMixBox
     int n_tiles;
@@ -58,6 +57,9 @@ struct MixShape {
     int r, warps, tile;
 };
 MixShape mix_shape(int mode);
+size_t sparse_smem_bytes(int buf_elems, int elem_bytes, int rec_bytes, int stages);
+cudaError_t launch_sparse_tmem(int dtype, const CUtensorMap &tmap, const MixArgs &a, int grid,
+                               size_t smem, cudaStream_t st);
 size_t mix_smem_bytes(int buf_elems, int elem_bytes, int rec_bytes, int stages);
 // tmap: 2-D tiled tensor map over the sources ({len, n_src}, box {kMixBox, 1}, zero fill)
 cudaError_t launch_mix(int mode, int dtype, const CUtensorMap &tmap, const MixArgs &a, int grid,
@@ -122,7 +124,7 @@ cudaError_t launch_fft_out(const FftOutArgs &a, int n_frames, cudaStream_t st);
 cudaError_t launch_topk(const float *g, int n_rows, int refl_len, int k, uint16_t *idx, float *w,
                         uint8_t *nnz, cudaStream_t st);
 cudaError_t launch_build_sparse_records(const uint16_t *idx, const float *w, const uint8_t *nnz,
-                                        int n_dirs, int k_max, int R, int nch_pad,
+                                        int n_dirs, int k_max, int seg_len, int n_seg, int nseg_pad,
                                         unsigned char *rec, int rec_bytes, cudaStream_t st);
 cudaError_t launch_build_dense_records(const uint16_t *idx, const float *w, const uint8_t *nnz,
                                        int n_dirs, int k_max, const float *res, int res_len,

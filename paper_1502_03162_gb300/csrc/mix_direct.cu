@@ -1,30 +1,26 @@
-// mix_direct.cu -- direct-convolution mixing kernels for sm_103a.
-//
-//   sparse (the method, Eq. 2 with the resonance moved after the mix):
-//       z_e[n] = sum_s sum_k w_{d(s),e,k} * y_s[n - i_{d(s),e,k}]
-//   dense (plain method, direct convolution with the dense HRIR x = f * g, Eq. 1):
-//       out_e[n] = sum_s sum_j x_{d(s),e}[j] * y_s[n - j]
-// Both follow the direct-convolution definition of Sec. I footnote 2 (0-based).
+// mix_direct.cu -- dense-HRIR direct-convolution mixing kernel for sm_103a (plain method 1):
+//       out_e[n] = sum_s sum_j x_{d(s),e}[j] * y_s[n - j],   x = f * g  (Eq. 1)
+// following the direct-convolution definition of Sec. I footnote 2 (0-based).  The sparse
+// method's kernel (mix_sparse_tmem.cu) shares the staging, partition and flush scheme.
 //
 // Design (one CTA per SM, persistent, balanced contiguous ranges of (tile, source) units):
 //  * warp 0 streams each source's tile [t0 - halo, t0 + TILE) into a shared-memory ring
 //    with 2-D tensor TMA boxes (cp.async.bulk.tensor + mbarrier complete_tx; samples
 //    outside [0, len) arrive as hardware zero fill), plus the direction's filter record
 //    as a 1-D bulk copy in the same stage;
-//  * all warps compute; each owns 32 lanes x R consecutive outputs per lane and keeps
-//    a 2R-sample register window of the source: for filter taps with offsets in chunk c,
+//  * all warps compute; each owns 32 lanes x R = 36 consecutive outputs per lane and keeps
+//    a 2R-sample register window of the source: for the HRIR taps of chunk c, offsets
 //    [cR, cR + R), output n + r needs y[n + r - cR - delta] = win[R - delta + r], a fixed
-//    register for each (delta, r).  A warp-uniform indirect jump on (ear, delta) picks the
-//    code path, so each tap costs R FMAs with no shared-memory traffic; moving to the next
-//    chunk reuses half the window and loads R fresh samples (conflict-free LDS.128: the
-//    lane stride of R floats is an odd number of 16-byte bank groups);
+//    register for each (delta, r), so the fully unrolled chunk is 2 x R x R FMAs with the
+//    tap weights broadcast from shared memory; moving to the next chunk reuses half the
+//    window and loads R fresh samples (conflict-free LDS.128: the lane stride of R floats
+//    is an odd number of 16-byte bank groups);
 //  * register accumulators are flushed every <= 64 sources into partial slots that the
 //    reduction kernel sums in a fixed order (deterministic, bounded FP32 error).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "kernels.h"
-#include "tap_dispatch.cuh"
 
 namespace hrir {
 
@@ -83,46 +79,6 @@ struct Window<__half, R> {
         }
     }
 };
-
-// ---- taps of the sparse filter: acc[r] += w * y[n + r - (cR + delta)] --------------------
-// With lo = y[n - (c+1)R .. n - cR) and hi = y[n - cR .. n - cR + R), the sample for output
-// r is window index R - delta + r.  TapChunk<R> (generated inline PTX) runs all taps of a
-// chunk, one brx.idx.uni jump per tap into 2R straight-line FMA blocks.
-
-// Sparse record (built for chunks of R offsets): int4 {n_taps, c_top, c_bot, 0}, u16
-// cnt[nch_pad], then int2 {code, weight bits} per tap in descending chunk order.  The window
-// slides from chunk c_top down to c_bot (later in time); the two halves swap roles each step
-// (A/B ping-pong), so only the R fresh samples are loaded and nothing is moved.
-template <typename T, int R>
-__device__ __forceinline__ void sparse_source(const T *yb, int halo, int lane_off, int nch_pad,
-                                              const unsigned char *rec, float (&accL)[R],
-                                              float (&accR)[R])
-{
-    const int4 hdr = *reinterpret_cast<const int4 *>(rec);
-    if (hdr.x <= 0) return;
-    const uint16_t *cnt = reinterpret_cast<const uint16_t *>(rec + 16);
-    uint32_t taps = smem_addr(rec + 16 + 2 * nch_pad);
-    int c = hdr.y;
-    const int c_bot = hdr.z;
-    const T *base = yb + halo + lane_off;
-    float A[R], B[R];
-    Window<T, R>::load(base - (c + 1) * R, A);
-    Window<T, R>::load(base - c * R, B);
-    while (true) {
-        int n = cnt[c];
-        if (n) TapChunk<R>::run(A, B, accL, accR, taps, n);
-        taps += 8u * n;
-        if (c == c_bot) break;
-        --c;
-        Window<T, R>::load(base - c * R, A);
-        n = cnt[c];
-        if (n) TapChunk<R>::run(B, A, accL, accR, taps, n);
-        taps += 8u * n;
-        if (c == c_bot) break;
-        --c;
-        Window<T, R>::load(base - c * R, B);
-    }
-}
 
 // Dense record: float h[2][nchunk * R] (the HRIR of each ear, zero padded).
 template <typename T, int R>
@@ -264,11 +220,8 @@ __global__ void __launch_bounds__(NW * 32, 1)
             break;
         const T *yb = ybuf + (size_t)st * a.buf_elems;
         const unsigned char *rec = rbuf + (size_t)st * a.rec_bytes;
-        if constexpr (MODE == MIX_SPARSE)
-            sparse_source<T, R>(yb, a.halo, lane_off, a.nchunk, rec, accL, accR);
-        else
-            dense_source<T, R>(yb, a.halo, lane_off, a.nchunk, reinterpret_cast<const float *>(rec),
-                               accL, accR);
+        dense_source<T, R>(yb, a.halo, lane_off, a.nchunk, reinterpret_cast<const float *>(rec),
+                           accL, accR);
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&bars[stages + st]));
         ++run_n;
@@ -336,8 +289,7 @@ static cudaError_t launch_dtype(int dtype, const CUtensorMap &tmap, const MixArg
 cudaError_t launch_mix(int mode, int dtype, const CUtensorMap &tmap, const MixArgs &a, int grid,
                        size_t smem, cudaStream_t st)
 {
-    if (mode == MIX_SPARSE)
-        return launch_dtype<MIX_SPARSE, kSparseR, kSparseWarps>(dtype, tmap, a, grid, smem, st);
+    if (mode == MIX_SPARSE) return launch_sparse_tmem(dtype, tmap, a, grid, smem, st);
     return launch_dtype<MIX_DENSE, kDenseR, kDenseWarps>(dtype, tmap, a, grid, smem, st);
 }
 

@@ -80,7 +80,7 @@ extern "C" int hrir_render_batch_noalloc(hrir_ctx *ctx, int n_src, int64_t len, 
     const MixShape shape = mix_shape(sparse ? MIX_SPARSE : MIX_DENSE);
     const int tile = shape.tile;
     const int nchunk = sparse ? ctx->sparse_nchunk : ctx->dense_nchunk;
-    const int halo = (int)round_up((int64_t)nchunk * shape.r, 8);
+    const int halo = (int)round_up((int64_t)nchunk * (sparse ? kSparseSegment : shape.r), 8);
     const int buf_elems = (int)round_up(halo + tile, kMixBox);
     const int rec_bytes = sparse ? ctx->sparse_rec_bytes : 2 * ctx->dense_padded * 4;
     const int64_t mix_len = sparse ? std::min<int64_t>(out_len, len + ctx->refl_len - 1) : out_len;

@@ -83,49 +83,46 @@ __global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, 
 }
 
 // ---- sparse records ------------------------------------------------------------------------
-// Record of one direction for window chunks of R offsets:
-//   int4  {n_taps, c_top, c_bot, 0}         (c_top/c_bot: chunks of the largest/smallest offset)
-//   u16   cnt[nch_pad]                      (taps per chunk)
-//   int2  tap[n_taps] {code, weight bits}   (code = offset - cR + R * ear; chunks descending)
-// Both ears' ascending tap lists are merged from their ends, which yields descending offsets
-// and therefore descending chunks.
+// Record of one direction for the tensor-memory sparse kernel, whose window covers one
+// segment of seg_len filter offsets at a time:
+//   int4  {n_seg, 0, 0, 0}
+//   int2  cnt[nseg_pad] {left taps, right taps} of each segment
+//   int2  tap[...] {TMEM column, weight bits}: per segment, its left then its right taps
+// A tap at offset o of segment s reads window columns (s+1) seg_len - o onward.
 __global__ void build_sparse_records_kernel(const uint16_t *__restrict__ idx,
                                             const float *__restrict__ w,
                                             const uint8_t *__restrict__ nnz, int n_dirs, int k_max,
-                                            int R, int nch_pad, unsigned char *__restrict__ rec,
-                                            int rec_bytes)
+                                            int seg_len, int n_seg, int nseg_pad,
+                                            unsigned char *__restrict__ rec, int rec_bytes)
 {
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
     if (d > n_dirs) return;
     unsigned char *r0 = rec + (size_t)d * rec_bytes;
     int4 *hdr = reinterpret_cast<int4 *>(r0);
-    uint16_t *cnt = reinterpret_cast<uint16_t *>(r0 + 16);
-    int2 *taps = reinterpret_cast<int2 *>(r0 + 16 + 2 * nch_pad);
-    for (int c = 0; c < nch_pad; ++c) cnt[c] = 0;
+    int2 *cnt = reinterpret_cast<int2 *>(r0 + 16);
+    int2 *taps = reinterpret_cast<int2 *>(r0 + 16 + 8 * nseg_pad);
+    for (int c = 0; c < nseg_pad; ++c) cnt[c] = make_int2(0, 0);
     if (d == n_dirs) {  // the silent record used for out-of-range direction ids
         *hdr = make_int4(0, 0, 0, 0);
         return;
     }
-    const size_t rl = ((size_t)d * 2 + 0) * k_max, rr = ((size_t)d * 2 + 1) * k_max;
-    int il = (int)nnz[(size_t)d * 2 + 0] - 1, ir = (int)nnz[(size_t)d * 2 + 1] - 1;
-    const int n = il + ir + 2;
-    int c_top = 0, c_bot = 0;
-    for (int o = 0; o < n; ++o) {
-        bool take_left;
-        if (il < 0) take_left = false;
-        else if (ir < 0) take_left = true;
-        else take_left = idx[rl + il] >= idx[rr + ir];
-        const int i = take_left ? (int)idx[rl + il] : (int)idx[rr + ir];
-        const float wv = take_left ? w[rl + il] : w[rr + ir];
-        const int c = i / R;
-        if (o == 0) c_top = c;
-        c_bot = c;
-        cnt[c] += 1;
-        taps[o] = make_int2(i - c * R + (take_left ? 0 : R), __float_as_int(wv));
-        if (take_left) --il;
-        else --ir;
+    int o = 0;
+    for (int s = 0; s < n_seg; ++s) {
+        const int lo = s * seg_len, hi = lo + seg_len;
+        int n_e[2] = {0, 0};
+        for (int e = 0; e < 2; ++e) {
+            const size_t row = ((size_t)d * 2 + e) * k_max;
+            const int k = nnz[(size_t)d * 2 + e];
+            for (int t = 0; t < k; ++t) {
+                const int i = idx[row + t];
+                if (i < lo || i >= hi) continue;
+                taps[o++] = make_int2(hi - i, __float_as_int(w[row + t]));
+                ++n_e[e];
+            }
+        }
+        cnt[s] = make_int2(n_e[0], n_e[1]);
     }
-    *hdr = make_int4(n, c_top, c_bot, 0);
+    *hdr = make_int4(n_seg, 0, 0, 0);
 }
 
 // ---- dense HRIRs: x_{d,e}[n] = sum_t w_t f_e[n - idx_t] (Eq. 1), zero padded -------------
@@ -167,12 +164,12 @@ cudaError_t launch_topk(const float *g, int n_rows, int refl_len, int k, uint16_
 }
 
 cudaError_t launch_build_sparse_records(const uint16_t *idx, const float *w, const uint8_t *nnz,
-                                        int n_dirs, int k_max, int R, int nch_pad,
+                                        int n_dirs, int k_max, int seg_len, int n_seg, int nseg_pad,
                                         unsigned char *rec, int rec_bytes, cudaStream_t st)
 {
     const int n = n_dirs + 1;
-    build_sparse_records_kernel<<<(n + 127) / 128, 128, 0, st>>>(idx, w, nnz, n_dirs, k_max, R,
-                                                                nch_pad, rec, rec_bytes);
+    build_sparse_records_kernel<<<(n + 127) / 128, 128, 0, st>>>(
+        idx, w, nnz, n_dirs, k_max, seg_len, n_seg, nseg_pad, rec, rec_bytes);
     return cudaGetLastError();
 }
 
