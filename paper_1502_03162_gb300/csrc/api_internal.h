@@ -64,6 +64,10 @@ int pick_stages(int buf_elems, int elem_bytes, int rec_bytes, size_t *smem);
 // 2-D tensor map over the sources: dims {len, n_src}, row stride ld, box {kMixBox, 1}.
 int make_source_map(hrir_ctx *ctx, CUtensorMap *m, const void *src, int dt, int64_t len,
                     int64_t ld, int n_src, int box_rows = 1);
+// 3-D view of the sources {kMixBox, len / kMixBox, n_src} with box {kMixBox, box_rows, 1};
+// when len < kMixBox there are no full rows and *m is a copy of the 2-D map `fallback`.
+int make_source_map3(hrir_ctx *ctx, CUtensorMap *m, const CUtensorMap &fallback, const void *src,
+                     int dt, int64_t len, int64_t ld, int n_src, int box_rows);
 cudaEvent_t take_event(hrir_ctx *ctx);
 
 // Brackets one kernel launch with events when timing is enabled.

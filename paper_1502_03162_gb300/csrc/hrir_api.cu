@@ -130,6 +130,31 @@ int make_source_map(hrir_ctx *ctx, CUtensorMap *m, const void *src, int dt, int6
     return HRIR_OK;
 }
 
+int make_source_map3(hrir_ctx *ctx, CUtensorMap *m, const CUtensorMap &fallback, const void *src,
+                     int dt, int64_t len, int64_t ld, int n_src, int box_rows)
+{
+    const int64_t rows = len / kMixBox;
+    if (rows == 0) {
+        *m = fallback;
+        return HRIR_OK;
+    }
+    auto fn = tensor_map_encoder();
+    if (!fn) return fail(ctx, HRIR_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    const CUtensorMapDataType ty = dt == HRIR_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : dt == HRIR_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const int64_t es = (int64_t)dtype_size(dt);
+    const cuuint64_t dims[3] = {(cuuint64_t)kMixBox, (cuuint64_t)rows, (cuuint64_t)n_src};
+    const cuuint64_t strides[2] = {(cuuint64_t)(kMixBox * es), (cuuint64_t)(ld * es)};
+    const cuuint32_t box[3] = {(cuuint32_t)kMixBox, (cuuint32_t)box_rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, ty, 3, const_cast<void *>(src), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, HRIR_ECUDA, "cuTensorMapEncodeTiled (3-D) failed (%d)", (int)r);
+    return HRIR_OK;
+}
+
 cudaEvent_t take_event(hrir_ctx *ctx)
 {
     if (!ctx->free_events.empty()) {
@@ -485,7 +510,8 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
     const int nchunk = sparse ? ctx->sparse_nchunk : ctx->dense_nchunk;
     const MixShape shape = mix_shape(sparse ? MIX_SPARSE : MIX_DENSE);
     const int tile = shape.tile;
-    const int halo = (int)round_up((int64_t)nchunk * (sparse ? kSparseSegment : shape.r), 8);
+    // history before each tile, a multiple of kMixBox so that tiles start on a source row
+    const int halo = (int)round_up((int64_t)nchunk * (sparse ? kSparseSegment : shape.r), kMixBox);
     const int buf_elems = (int)round_up(halo + tile, kMixBox);
     const int rec_bytes = sparse ? ctx->sparse_rec_bytes : 2 * ctx->dense_padded * 4;
     const int64_t mix_len = sparse ? std::min<int64_t>(out_len, len + ctx->refl_len - 1) : out_len;
@@ -493,8 +519,10 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
     size_t smem = 0;
     const int stages = pick_stages(buf_elems, (int)es, rec_bytes, &smem);
     if (stages == 0) return fail(ctx, HRIR_EINVAL, "filters too long for the shared-memory pipeline");
-    CUtensorMap tmap;
+    CUtensorMap tmap, tmap3;
     int rc = make_source_map(ctx, &tmap, src, (int)dt, len, src_ld, n_src);
+    if (rc) return rc;
+    rc = make_source_map3(ctx, &tmap3, tmap, src, (int)dt, len, src_ld, n_src, buf_elems / kMixBox);
     if (rc) return rc;
 
     Partition part;
@@ -520,6 +548,7 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
     a.nchunk = sparse ? ctx->sparse_nch_pad : nchunk;
     a.halo = halo;
     a.buf_elems = buf_elems;
+    a.full_rows = (int)(len / kMixBox);
     a.n_tiles = n_tiles;
     a.stages = stages;
     a.part = part;
@@ -528,7 +557,8 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
     a.status = ctx->d_status;
     {
         KernelTimer kt(ctx, sparse ? HRIR_K_MIX_SPARSE : HRIR_K_MIX_DENSE, st);
-        CUDA_TRY(ctx, launch_mix(sparse ? MIX_SPARSE : MIX_DENSE, (int)dt, tmap, a, (int)part.P, smem, st));
+        CUDA_TRY(ctx, launch_mix(sparse ? MIX_SPARSE : MIX_DENSE, (int)dt, tmap, tmap3, a, (int)part.P,
+                                 smem, st));
         kt.done();
     }
 

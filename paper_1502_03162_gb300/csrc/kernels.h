@@ -45,6 +45,7 @@ struct MixArgs {
                                 // per-segment count array of a record (even)
     int halo;                   // >= nchunk * R samples of history per tile (multiple of 8)
     int buf_elems;              // per-stage source buffer, multiple of kMixBox
+    int full_rows;              // floor(len / kMixBox): rows of the 3-D source view
     int n_tiles;
     int stages;                 // pipeline depth (2..kMixMaxStages)
     Partition part;
@@ -58,12 +59,14 @@ struct MixShape {
 };
 MixShape mix_shape(int mode);
 size_t sparse_smem_bytes(int buf_elems, int elem_bytes, int rec_bytes, int stages);
-cudaError_t launch_sparse_tmem(int dtype, const CUtensorMap &tmap, const MixArgs &a, int grid,
-                               size_t smem, cudaStream_t st);
+cudaError_t launch_sparse_tmem(int dtype, const CUtensorMap &tmap, const CUtensorMap &tmap3,
+                               const MixArgs &a, int grid, size_t smem, cudaStream_t st);
 size_t mix_smem_bytes(int buf_elems, int elem_bytes, int rec_bytes, int stages);
-// tmap: 2-D tiled tensor map over the sources ({len, n_src}, box {kMixBox, 1}, zero fill)
-cudaError_t launch_mix(int mode, int dtype, const CUtensorMap &tmap, const MixArgs &a, int grid,
-                       size_t smem, cudaStream_t st);
+// tmap: 2-D tiled tensor map over the sources ({len, n_src}, box {kMixBox, 1}, zero fill);
+// tmap3: 3-D view {kMixBox, len / kMixBox, n_src} with box {kMixBox, buf_elems / kMixBox, 1}
+// that loads a whole tile in one request when the tile lies within the full rows.
+cudaError_t launch_mix(int mode, int dtype, const CUtensorMap &tmap, const CUtensorMap &tmap3,
+                       const MixArgs &a, int grid, size_t smem, cudaStream_t st);
 
 // ---- fixed-order reduction of partial slots + optional resonance FIR -------------------
 struct ReduceArgs {

@@ -117,9 +117,10 @@ __device__ __forceinline__ void dense_source(const T *yb, int halo, int lane_off
 // the source tile [t0 - halo, t0 - halo + buf_elems) as kMixBox-wide tensor-TMA boxes
 // (out-of-range samples arrive as zeros) and the direction's filter record.
 template <typename T>
-__device__ __forceinline__ void issue_unit(const CUtensorMap *tmap, const MixArgs &a, int64_t u,
-                                           int d, T *ybuf, unsigned char *rbuf, uint32_t full_bar,
-                                           int lane, int tile)
+__device__ __forceinline__ void issue_unit(const CUtensorMap *tmap, const CUtensorMap *tmap3,
+                                           const MixArgs &a, int64_t u, int d, T *ybuf,
+                                           unsigned char *rbuf, uint32_t full_bar, int lane,
+                                           int tile)
 {
     const int t = (int)(u / a.n_src);
     const int s = (int)(u - (int64_t)t * a.n_src);
@@ -128,8 +129,16 @@ __device__ __forceinline__ void issue_unit(const CUtensorMap *tmap, const MixArg
     if (lane == 0)
         mbar_arrive_expect_tx(full_bar, (uint32_t)(a.buf_elems * sizeof(T) + a.rec_bytes));
     __syncwarp();
-    for (int b = lane; b < n_box; b += 32)
-        tma_load_2d(smem_addr(ybuf + b * kMixBox), tmap, x0 + b * kMixBox, s, full_bar);
+    // The tile starts on a row of the 3-D view (x0 % kMixBox == 0); when every row it covers
+    // is a full row of the source, one request loads it (rows before the source read as
+    // zeros).  Tiles that reach the ragged last row use one-row boxes of the 2-D map.
+    const int r0 = x0 >= 0 ? x0 / kMixBox : -((-x0 + kMixBox - 1) / kMixBox);
+    if (r0 + n_box <= a.full_rows) {
+        if (lane == 0) tma_load_3d(smem_addr(ybuf), tmap3, 0, r0, s, full_bar);
+    } else {
+        for (int b = lane; b < n_box; b += 32)
+            tma_load_2d(smem_addr(ybuf + b * kMixBox), tmap, x0 + b * kMixBox, s, full_bar);
+    }
     if (lane == 0)
         tma_load_1d(smem_addr(rbuf), a.table + (size_t)d * a.rec_bytes, (uint32_t)a.rec_bytes,
                     full_bar);
@@ -149,7 +158,8 @@ __device__ __forceinline__ int unit_dir(const MixArgs &a, int64_t u, int lane)
 
 template <int MODE, typename T, int R, int NW>
 __global__ void __launch_bounds__(NW * 32, 1)
-    mix_kernel(const __grid_constant__ CUtensorMap tmap, const MixArgs a)
+    mix_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap3,
+               const MixArgs a)
 {
     constexpr int kTile = NW * 32 * R;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -162,6 +172,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         prefetch_tensormap(&tmap);
+        prefetch_tensormap(&tmap3);
         for (int i = 0; i < stages; ++i) {
             mbar_init(smem_addr(&bars[i]), 1);                   // full: producer + tx bytes
             mbar_init(smem_addr(&bars[stages + i]), NW);  // empty: one arrive per warp
@@ -182,7 +193,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
         const int64_t n0 = n_units < stages ? n_units : stages;
         for (int64_t i = 0; i < n0; ++i) {
             const int d = unit_dir(a, u_begin + i, lane);
-            issue_unit<T>(&tmap, a, u_begin + i, d, ybuf + (size_t)i * a.buf_elems,
+            issue_unit<T>(&tmap, &tmap3, a, u_begin + i, d, ybuf + (size_t)i * a.buf_elems,
                           rbuf + (size_t)i * a.rec_bytes, smem_addr(&bars[i]), lane, kTile);
         }
         issued = n0;
@@ -203,7 +214,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
             const int st = (int)((k - 1) % stages);
             const uint32_t par = (uint32_t)(((k - 1) / stages) & 1);
             if (!mbar_wait_bounded(smem_addr(&bars[stages + st]), par, abort_flag, a.status)) break;
-            issue_unit<T>(&tmap, a, u_begin + issued, next_dir, ybuf + (size_t)st * a.buf_elems,
+            issue_unit<T>(&tmap, &tmap3, a, u_begin + issued, next_dir, ybuf + (size_t)st * a.buf_elems,
                           rbuf + (size_t)st * a.rec_bytes, smem_addr(&bars[st]), lane, kTile);
             ++issued;
             if (issued < n_units) next_dir = unit_dir(a, u_begin + issued, lane);
@@ -267,30 +278,30 @@ MixShape mix_shape(int mode)
 }
 
 template <int MODE, typename T, int R, int NW>
-static cudaError_t launch_one(const CUtensorMap &tmap, const MixArgs &a, int grid, size_t smem,
-                              cudaStream_t st)
+static cudaError_t launch_one(const CUtensorMap &tmap, const CUtensorMap &tmap3, const MixArgs &a,
+                              int grid, size_t smem, cudaStream_t st)
 {
     auto k = mix_kernel<MODE, T, R, NW>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, NW * 32, smem, st>>>(tmap, a);
+    k<<<grid, NW * 32, smem, st>>>(tmap, tmap3, a);
     return cudaGetLastError();
 }
 
 template <int MODE, int R, int NW>
-static cudaError_t launch_dtype(int dtype, const CUtensorMap &tmap, const MixArgs &a, int grid,
-                                size_t smem, cudaStream_t st)
+static cudaError_t launch_dtype(int dtype, const CUtensorMap &tmap, const CUtensorMap &tmap3,
+                                const MixArgs &a, int grid, size_t smem, cudaStream_t st)
 {
-    if (dtype == 0) return launch_one<MODE, float, R, NW>(tmap, a, grid, smem, st);
-    if (dtype == 1) return launch_one<MODE, __nv_bfloat16, R, NW>(tmap, a, grid, smem, st);
-    return launch_one<MODE, __half, R, NW>(tmap, a, grid, smem, st);
+    if (dtype == 0) return launch_one<MODE, float, R, NW>(tmap, tmap3, a, grid, smem, st);
+    if (dtype == 1) return launch_one<MODE, __nv_bfloat16, R, NW>(tmap, tmap3, a, grid, smem, st);
+    return launch_one<MODE, __half, R, NW>(tmap, tmap3, a, grid, smem, st);
 }
 
-cudaError_t launch_mix(int mode, int dtype, const CUtensorMap &tmap, const MixArgs &a, int grid,
-                       size_t smem, cudaStream_t st)
+cudaError_t launch_mix(int mode, int dtype, const CUtensorMap &tmap, const CUtensorMap &tmap3,
+                       const MixArgs &a, int grid, size_t smem, cudaStream_t st)
 {
-    if (mode == MIX_SPARSE) return launch_sparse_tmem(dtype, tmap, a, grid, smem, st);
-    return launch_dtype<MIX_DENSE, kDenseR, kDenseWarps>(dtype, tmap, a, grid, smem, st);
+    if (mode == MIX_SPARSE) return launch_sparse_tmem(dtype, tmap, tmap3, a, grid, smem, st);
+    return launch_dtype<MIX_DENSE, kDenseR, kDenseWarps>(dtype, tmap, tmap3, a, grid, smem, st);
 }
 
 }  // namespace hrir

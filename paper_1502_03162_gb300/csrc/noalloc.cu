@@ -80,7 +80,8 @@ extern "C" int hrir_render_batch_noalloc(hrir_ctx *ctx, int n_src, int64_t len, 
     const MixShape shape = mix_shape(sparse ? MIX_SPARSE : MIX_DENSE);
     const int tile = shape.tile;
     const int nchunk = sparse ? ctx->sparse_nchunk : ctx->dense_nchunk;
-    const int halo = (int)round_up((int64_t)nchunk * (sparse ? kSparseSegment : shape.r), 8);
+    // history before each tile, a multiple of kMixBox so that tiles start on a source row
+    const int halo = (int)round_up((int64_t)nchunk * (sparse ? kSparseSegment : shape.r), kMixBox);
     const int buf_elems = (int)round_up(halo + tile, kMixBox);
     const int rec_bytes = sparse ? ctx->sparse_rec_bytes : 2 * ctx->dense_padded * 4;
     const int64_t mix_len = sparse ? std::min<int64_t>(out_len, len + ctx->refl_len - 1) : out_len;
@@ -104,8 +105,10 @@ extern "C" int hrir_render_batch_noalloc(hrir_ctx *ctx, int n_src, int64_t len, 
     size_t smem = 0;
     const int stages = pick_stages(buf_elems, (int)es, rec_bytes, &smem);
     if (stages == 0) return fail(ctx, HRIR_EINVAL, "filters too long for the shared-memory pipeline");
-    CUtensorMap tmap;
+    CUtensorMap tmap, tmap3;
     rc = make_source_map(ctx, &tmap, src, (int)dt, len, src_ld, n_src);
+    if (rc) return rc;
+    rc = make_source_map3(ctx, &tmap3, tmap, src, (int)dt, len, src_ld, n_src, buf_elems / kMixBox);
     if (rc) return rc;
 
     // Every partial slot the reduction reads is written by the mixing kernel of this same
@@ -122,14 +125,15 @@ extern "C" int hrir_render_batch_noalloc(hrir_ctx *ctx, int n_src, int64_t len, 
     a.nchunk = sparse ? ctx->sparse_nch_pad : nchunk;
     a.halo = halo;
     a.buf_elems = buf_elems;
+    a.full_rows = (int)(len / kMixBox);
     a.n_tiles = n_tiles;
     a.stages = stages;
     a.part = part;
     a.partial = scratch;
     a.slots = slots;
     a.status = ctx->d_status;
-    HRIR_CUDA_TRY(ctx, launch_mix(sparse ? MIX_SPARSE : MIX_DENSE, (int)dt, tmap, a, (int)part.P,
-                                  smem, st));
+    HRIR_CUDA_TRY(ctx, launch_mix(sparse ? MIX_SPARSE : MIX_DENSE, (int)dt, tmap, tmap3, a,
+                                  (int)part.P, smem, st));
     ReduceArgs r;
     r.partial = scratch;
     r.slots = slots;
