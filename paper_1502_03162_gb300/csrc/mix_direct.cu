@@ -144,11 +144,15 @@ __device__ __forceinline__ void issue_unit(const CUtensorMap *tmap, const CUtens
                     full_bar);
 }
 
-// Direction record index of unit u (the silent record for an id out of range).
-__device__ __forceinline__ int unit_dir(const MixArgs &a, int64_t u, int lane)
+// Raw direction id of unit u (the load stays in flight until checked_dir uses it).
+__device__ __forceinline__ int raw_dir(const MixArgs &a, int64_t u)
 {
-    const int s = (int)(u % a.n_src);
-    int d = __ldg(a.dir + s);
+    return __ldg(a.dir + (int)(u % a.n_src));
+}
+
+// Record index for a direction id: the silent record for an id out of range.
+__device__ __forceinline__ int checked_dir(const MixArgs &a, int d, int lane)
+{
     if ((unsigned)d >= (unsigned)a.n_dirs) {
         if (lane == 0) atomicOr(a.status, DEV_BAD_DIR);
         d = a.n_dirs;
@@ -192,12 +196,12 @@ __global__ void __launch_bounds__(NW * 32, 1)
     if (warp == 0) {
         const int64_t n0 = n_units < stages ? n_units : stages;
         for (int64_t i = 0; i < n0; ++i) {
-            const int d = unit_dir(a, u_begin + i, lane);
+            const int d = checked_dir(a, raw_dir(a, u_begin + i), lane);
             issue_unit<T>(&tmap, &tmap3, a, u_begin + i, d, ybuf + (size_t)i * a.buf_elems,
                           rbuf + (size_t)i * a.rec_bytes, smem_addr(&bars[i]), lane, kTile);
         }
         issued = n0;
-        if (issued < n_units) next_dir = unit_dir(a, u_begin + issued, lane);
+        if (issued < n_units) next_dir = raw_dir(a, u_begin + issued);
     }
 
     const int lane_off = (warp * 32 + lane) * R;
@@ -214,10 +218,11 @@ __global__ void __launch_bounds__(NW * 32, 1)
             const int st = (int)((k - 1) % stages);
             const uint32_t par = (uint32_t)(((k - 1) / stages) & 1);
             if (!mbar_wait_bounded(smem_addr(&bars[stages + st]), par, abort_flag, a.status)) break;
-            issue_unit<T>(&tmap, &tmap3, a, u_begin + issued, next_dir, ybuf + (size_t)st * a.buf_elems,
-                          rbuf + (size_t)st * a.rec_bytes, smem_addr(&bars[st]), lane, kTile);
+            issue_unit<T>(&tmap, &tmap3, a, u_begin + issued, checked_dir(a, next_dir, lane),
+                          ybuf + (size_t)st * a.buf_elems, rbuf + (size_t)st * a.rec_bytes,
+                          smem_addr(&bars[st]), lane, kTile);
             ++issued;
-            if (issued < n_units) next_dir = unit_dir(a, u_begin + issued, lane);
+            if (issued < n_units) next_dir = raw_dir(a, u_begin + issued);
         }
         const int t = (int)(u / a.n_src);
         if (t != cur_t) {

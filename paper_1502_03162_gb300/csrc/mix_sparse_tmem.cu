@@ -146,36 +146,37 @@ __device__ __forceinline__ void fma_slice(float (&acc)[R], const uint32_t (&v)[R
     for (int r = 0; r < R; ++r) acc[r] = fmaf(w, __uint_as_float(v[r]), acc[r]);
 }
 
-// Apply n taps {column, weight bits} to acc, double-buffered loads.
+// Apply n taps {column, weight bits} to acc.  TMEM loads are double-buffered (the next
+// tap's slice is in flight while the current tap's FMAs issue) and tap records are read
+// from shared memory two taps ahead, so no load feeds an address right away.
 __device__ __forceinline__ void apply_taps(float (&acc)[R], uint32_t tw, const int2 *taps, int n)
 {
     if (n <= 0) return;
     uint32_t A[R], B[R];
-    int2 tp = taps[0];
-    tm_ld36(tw + (uint32_t)tp.x, A);
+    int2 cur = taps[0];
+    int2 nxt = n > 1 ? taps[1] : cur;
+    tm_ld36(tw + (uint32_t)cur.x, A);
+    int2 nn = n > 2 ? taps[2] : cur;
     tm_wait_ld(A);
-    float w = __int_as_float(tp.y);
     int t = 0;
     while (true) {
         bool more = t + 1 < n;
-        if (more) {
-            tp = taps[t + 1];
-            tm_ld36(tw + (uint32_t)tp.x, B);
-        }
-        fma_slice(acc, A, w);
+        if (more) tm_ld36(tw + (uint32_t)nxt.x, B);
+        fma_slice(acc, A, __int_as_float(cur.y));
         if (!more) break;
+        cur = nxt;
+        nxt = nn;
+        nn = t + 3 < n ? taps[t + 3] : cur;
         tm_wait_ld(B);
-        w = __int_as_float(tp.y);
         ++t;
         more = t + 1 < n;
-        if (more) {
-            tp = taps[t + 1];
-            tm_ld36(tw + (uint32_t)tp.x, A);
-        }
-        fma_slice(acc, B, w);
+        if (more) tm_ld36(tw + (uint32_t)nxt.x, A);
+        fma_slice(acc, B, __int_as_float(cur.y));
         if (!more) break;
+        cur = nxt;
+        nxt = nn;
+        nn = t + 3 < n ? taps[t + 3] : cur;
         tm_wait_ld(A);
-        w = __int_as_float(tp.y);
         ++t;
     }
 }
@@ -208,10 +209,15 @@ __device__ __forceinline__ void issue_unit(const CUtensorMap *tmap, const CUtens
                     full_bar);
 }
 
-__device__ __forceinline__ int unit_dir(const MixArgs &a, int64_t u, int lane)
+// Raw direction id of unit u (the load stays in flight until checked_dir uses it).
+__device__ __forceinline__ int raw_dir(const MixArgs &a, int64_t u)
 {
-    const int s = (int)(u % a.n_src);
-    int d = __ldg(a.dir + s);
+    return __ldg(a.dir + (int)(u % a.n_src));
+}
+
+// Record index for a direction id: the silent record for an id out of range.
+__device__ __forceinline__ int checked_dir(const MixArgs &a, int d, int lane)
+{
     if ((unsigned)d >= (unsigned)a.n_dirs) {
         if (lane == 0) atomicOr(a.status, DEV_BAD_DIR);
         d = a.n_dirs;
@@ -267,12 +273,12 @@ __global__ void __launch_bounds__(NW * 32, 1)
     if (warp == 0) {
         const int64_t n0 = n_units < stages ? n_units : stages;
         for (int64_t i = 0; i < n0; ++i) {
-            const int d = unit_dir(a, u_begin + i, lane);
+            const int d = checked_dir(a, raw_dir(a, u_begin + i), lane);
             issue_unit<T>(&tmap, &tmap3, a, u_begin + i, d, ybuf + (size_t)i * a.buf_elems,
                           rbuf + (size_t)i * a.rec_bytes, smem_addr(&bars[i]), lane);
         }
         issued = n0;
-        if (issued < n_units) next_dir = unit_dir(a, u_begin + issued, lane);
+        if (issued < n_units) next_dir = raw_dir(a, u_begin + issued);
     }
 
     const int lane_off = (warp * 32 + lane) * R;
@@ -287,10 +293,11 @@ __global__ void __launch_bounds__(NW * 32, 1)
             const int st = (int)((k - 1) % stages);
             const uint32_t par = (uint32_t)(((k - 1) / stages) & 1);
             if (!mbar_wait_bounded(smem_addr(&bars[stages + st]), par, abort_flag, a.status)) break;
-            issue_unit<T>(&tmap, &tmap3, a, u_begin + issued, next_dir, ybuf + (size_t)st * a.buf_elems,
-                          rbuf + (size_t)st * a.rec_bytes, smem_addr(&bars[st]), lane);
+            issue_unit<T>(&tmap, &tmap3, a, u_begin + issued, checked_dir(a, next_dir, lane),
+                          ybuf + (size_t)st * a.buf_elems, rbuf + (size_t)st * a.rec_bytes,
+                          smem_addr(&bars[st]), lane);
             ++issued;
-            if (issued < n_units) next_dir = unit_dir(a, u_begin + issued, lane);
+            if (issued < n_units) next_dir = raw_dir(a, u_begin + issued);
         }
         const int t = (int)(u / a.n_src);
         if (t != cur_t) {
