@@ -267,3 +267,58 @@ def topk(g, k: int):
     if rc != 0:
         raise ValueError(f"orc_topk rejected its arguments (rc={rc})")
     return idx, w, nnz
+
+
+# ---------------------------------------------------------------------------------------
+# moving sources: per-segment reflection filters, output-domain linear crossfade
+# ---------------------------------------------------------------------------------------
+def _sparse_at(y, idx, w, k, n0, n1):
+    """(y * g)[n] for n in [n0, n1) with g given by its k taps (zero outside y)."""
+    L = y.size
+    n = np.arange(n0, n1)
+    acc = np.zeros(n.size)
+    for t in range(k):
+        m = n - int(idx[t])
+        ok = (m >= 0) & (m < L)
+        acc[ok] += float(w[t]) * y[m[ok]]
+    return acc
+
+
+def render_moving(y, tap_idx, tap_w, tap_nnz, seg_len: int, refl_len: int, res, length=None):
+    """Binaural mix of moving sources (Eqs. 1-2 with a direction per segment).
+
+    y [S][ld] FP32; tap tables [S][n_seg][2][k] give the reflection filter g_{s,j,e} of
+    source s in segment j (samples [j seg_len, (j+1) seg_len)).  The reflection output of a
+    source at output sample n in segment j is the linear crossfade
+        z[n] = (1 - a) (y * g_{j-1})[n] + a (y * g_j)[n],   a = (n - j seg_len + 1) / seg_len
+    for 1 <= j < n_seg; segment 0 uses g_0 alone and every n >= n_seg seg_len (the filter
+    tails) uses g_{n_seg-1} alone.  Then out_e = f_e * sum_s z_{s,e}.  FP64 [2][L+H-1]."""
+    y = np.asarray(y)
+    if y.dtype != np.float32:
+        raise TypeError("sources are FP32")
+    S, ld = y.shape
+    L = int(ld if length is None else length)
+    tap_idx, tap_w, tap_nnz = np.asarray(tap_idx), np.asarray(tap_w), np.asarray(tap_nnz)
+    n_seg = tap_idx.shape[1]
+    assert tap_idx.shape[:3] == (S, n_seg, 2) and tap_nnz.shape == (S, n_seg, 2)
+    res = np.asarray(res, dtype=np.float64)
+    n_z = L + refl_len - 1
+    if L == 0:
+        return np.zeros((2, 0))
+    z = np.zeros((2, n_z))
+    for s in range(S):
+        ys = y[s, :L].astype(np.float64)
+        for j in range(max(n_seg, (n_z + seg_len - 1) // seg_len)):
+            n0, n1 = j * seg_len, min((j + 1) * seg_len, n_z)
+            if n0 >= n1:
+                break
+            jj = min(j, n_seg - 1)
+            for e in range(2):
+                cur = _sparse_at(ys, tap_idx[s, jj, e], tap_w[s, jj, e], int(tap_nnz[s, jj, e]), n0, n1)
+                if 1 <= j < n_seg:
+                    prev = _sparse_at(ys, tap_idx[s, j - 1, e], tap_w[s, j - 1, e],
+                                      int(tap_nnz[s, j - 1, e]), n0, n1)
+                    a = (np.arange(n0, n1) - n0 + 1) / seg_len
+                    cur = (1.0 - a) * prev + a * cur
+                z[e, n0:n1] += cur
+    return np.stack([conv_direct(res[e], z[e]) for e in range(2)])
