@@ -253,6 +253,105 @@ def bench_stream(rend, torch, block, warm_audio_s=10.0, audio_s=60.0, seed=12, r
             "arrivals_per_s": rate}
 
 
+def bench_learned(rend, torch, seed=13, S=4096, L=96000, seg=256, k=16, train_steps=20):
+    """Learned filters and moving sources (4096 sources x 2 s at 48 kHz, a direction every 256
+    samples, random-initialised network of the trained architecture): network inference for
+    every (source, segment, ear) row, top-k, and the crossfade render; plus the network's
+    training step (forward + backward + Adam) on one HRIR set's 1250 directions x 2 ears."""
+    from paper_1502_03162_gb300 import hrir, learned, synth
+    rng = np.random.default_rng(seed)
+    n_seg = (L + seg - 1) // seg
+    az, el = synth.trajectories(rng, S, n_seg)
+    rows = torch.from_numpy(learned.direction_rows(az, el)).cuda()
+    params = torch.from_numpy(learned.init_params(200, seed, 0.02)).cuda()
+    y = torch.from_numpy(synth.sources_ar1(rng, S, L)).cuda()
+    n_rows = rows.shape[0]
+    g = torch.empty((n_rows, 200), dtype=torch.float32, device="cuda")
+    idx = torch.empty((S, n_seg, 2, k), dtype=torch.int16, device="cuda")
+    w = torch.empty((S, n_seg, 2, k), dtype=torch.float32, device="cuda")
+    nnz = torch.empty((S, n_seg, 2), dtype=torch.uint8, device="cuda")
+    out = torch.empty((2, L + 230), dtype=torch.float32, device="cuda")
+    infer = lambda: hrir.hrir_mlp_forward(rend.ctx, rows, params, 200, out=g)  # noqa: E731
+    pack = lambda: hrir.hrir_topk_pack(rend.ctx, g.view(S, n_seg, 2, 200), k, idx, w, nnz)  # noqa: E731
+    render = lambda: hrir.hrir_render_moving(rend.ctx, y, idx, w, nnz, seg, out=out)  # noqa: E731
+    nb = lambda: None  # noqa: E731
+    t_inf = time_steps(infer, 3, 1, torch, nb)
+    t_pack = time_steps(pack, 3, 1, torch, nb)
+    t_ren = time_steps(render, 5, 2, torch, nb)
+    assert rend.sync() == 0
+    units = S * L * 2
+    # training step on one synthetic HRIR set's reflection rows
+    p = synth.hrir_set_params(4)
+    gaz, gel = synth.az_el_grid()
+    T = np.stack([synth.hrir_set_reflections(p, gaz, gel, np.full(gaz.size, e)) for e in range(2)],
+                 1).reshape(-1, 200).astype(np.float32)
+    trows = torch.from_numpy(learned.direction_rows(gaz, gel)).cuda()
+    tT = torch.from_numpy(T).cuda()
+    B = trows.shape[0]
+    acts = torch.empty((B, hrir.hrir_mlp_act_stride(200)), dtype=torch.float32, device="cuda")
+    tout = torch.empty((B, 200), dtype=torch.float32, device="cuda")
+    grads = torch.empty_like(params)
+    m, v = torch.zeros_like(params), torch.zeros_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    tp = params.clone()
+    step_no = [0]
+
+    def train_step():
+        step_no[0] += 1
+        hrir.hrir_mlp_forward(rend.ctx, trows, tp, 200, out=tout, acts=acts)
+        hrir.hrir_mlp_backward(rend.ctx, trows, tp, acts, tout, tT, 200, grads=grads, loss=loss)
+        hrir.hrir_mlp_adam(rend.ctx, tp, grads, m, v, step_no[0], 1e-3)
+    t_train = time_steps(train_step, train_steps, 3, torch, nb)
+    assert rend.sync() == 0
+    flops_fwd_row = 2 * (5 * 256 + 2 * 256 * 256 + 256 * 200)
+    return {"workload": f"moving: {S} sources x {L} samples, direction every {seg} samples, "
+                        f"network filters top-{k}, linear crossfade",
+            "render": {"value": units / (t_ren / 1e3), "unit": "source-ear samples/s",
+                       "ms": t_ren, "fp32_tflops": 4.0 * k * units / (t_ren / 1e3) / 1e12},
+            "filters": {"rows": n_rows, "ms": t_inf, "rows_per_s": n_rows / (t_inf / 1e3),
+                        "fp32_tflops": flops_fwd_row * n_rows / (t_inf / 1e3) / 1e12,
+                        "topk_ms": t_pack},
+            "end_to_end": {"value": units / ((t_inf + t_pack + t_ren) / 1e3),
+                           "unit": "source-ear samples/s", "ms": t_inf + t_pack + t_ren},
+            "train_step": {"rows": B, "ms": t_train, "steps_per_s": 1e3 / t_train,
+                           "fp32_tflops": 3 * flops_fwd_row * B / (t_train / 1e3) / 1e12}}
+
+
+def bench_precision(rend, torch, src, dirs, L, steps):
+    """BF16/FP16 source storage: the sparse mix (FP32 arithmetic) and the per-source resonance
+    on the tensor cores (Toeplitz-block GEMM, y * f for every source and ear)."""
+    from paper_1502_03162_gb300 import hrir
+    S = src.shape[0]
+    units = S * L * 2
+    out = torch.empty((2, L + 230), dtype=torch.float32, device="cuda")
+    nb = lambda: None  # noqa: E731
+    res = {}
+    for name, dt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        s16 = src.to(dt)
+        t = time_steps(lambda: rend.render(s16, dirs, mode="sparse", length=L, out=out),
+                       steps, 2, torch, nb)
+        res[f"sparse_{name}"] = {"value": units / (t / 1e3), "ms_per_step": t}
+        if name == "bf16":
+            u = torch.empty((S, 2, (L + 31 + 3) // 4 * 4), dtype=torch.float32, device="cuda")
+            rend.set_timing(True)
+            rend.kernel_times(reset=True)
+            t = time_steps(lambda: hrir.hrir_resonance_per_source(rend.ctx, s16, length=L, out=u),
+                           max(3, steps // 3), 1, torch, nb)
+            kt = rend.kernel_times(reset=True)
+            rend.set_timing(False)
+            kms = kt["resonance_gemm"][0] / max(kt["resonance_gemm"][1], 1)
+            bytes_alg = S * L * 2 + S * 2 * (L + 31) * 4
+            res["resonance_gemm_bf16"] = {
+                "value": units / (t / 1e3), "unit": "source-ear samples/s", "ms": t,
+                "kernel_ms": kms, "hbm_gbs": bytes_alg / (kms / 1e3) / 1e9,
+                "tensor_tflops": 768.0 * S * L / (kms / 1e3) / 1e12,
+                "useful_tflops": 128.0 * S * L / (kms / 1e3) / 1e12}
+            del u
+        del s16
+    assert rend.sync() == 0
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,7 +446,7 @@ def main():
         achieved = src_bytes / (mix_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak}
-    roof["traffic"] = profiled_traffic("mix_direct.cu", "mix_sparse_batched_1024x480000_k16.md")
+    roof["traffic"] = profiled_traffic("mix_sparse_tmem.cu", "mix_sparse_batched_1024x480000_k16.md")
     roof["peak_source"] = (f"FP32 FMA: {N_SM} SMs x {FP32_LANES} lanes x 2 x {sm_max:.0f} MHz "
                            f"(sm_max_mhz of {pk_kind} peaks); HBM {hbm_peak:.0f} GB/s {pk_kind}")
     roof["kernel_ms"] = mix_launch_ms
@@ -404,6 +503,11 @@ def main():
     result["e2e"] = {"value": units * world / (e2e_ms / 1e3), "unit": "source-ear samples/s",
                      "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(S * host.shape[1] * 4 + S * 4),
                      "d2h_bytes_per_step": int(2 * (L + 230) * 4)}
+
+    if not args.no_extras:
+        load(K_DEFAULT)
+        result["precision"] = bench_precision(rend, torch, src, dirs, L, max(3, args.steps // 5))
+        result["learned"] = bench_learned(rend, torch)
 
     if not args.no_stream:
         load(K_DEFAULT)

@@ -79,7 +79,8 @@ void hrir_destroy(hrir_ctx *ctx);
 const char *hrir_last_error(const hrir_ctx *ctx);
 
 /* Wait for all work enqueued on `stream`, then return and clear any device-side error flag:
- * HRIR_EINVAL (a direction id was out of range; that source was rendered as silence),
+ * HRIR_EINVAL (a direction id was out of range, that source rendered as silence, or a
+ * device tap table of hrir_render_moving held an invalid entry, which was ignored),
  * HRIR_ETIMEDOUT (a bounded wait expired; the output of that call is incomplete), or
  * HRIR_ECUDA if the stream reported a CUDA error. */
 int hrir_sync(hrir_ctx *ctx, void *stream);
@@ -196,7 +197,7 @@ int hrir_stream_close(hrir_ctx *ctx);
  * This call uses instead a fixed 32 MiB array of device memory that every GPU loading the
  * library holds until the process exits; it calls no cudaMalloc, cudaFree or other
  * allocating routine.  Renders whose partial sums need more than 32 MiB (about
- * n_tiles * ceil(n_src / 64 + 2) * 80 KiB, n_tiles = ceil((len + Lg - 1) / 10240) for
+ * n_tiles * ceil(n_src / 64 + 2) * 52 KiB, n_tiles = ceil((len + Lg - 1) / 6656) for
  * HRIR_SPARSE) are rejected with HRIR_EINVAL and a message giving the size needed.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  * with that device current); make that first call before any stream capture.  Every call
@@ -208,6 +209,85 @@ int hrir_render_batch_noalloc(hrir_ctx *ctx, int n_src, int64_t len, int64_t src
                               hrir_dtype dt, const void *src, const int32_t *dir,
                               hrir_mode mode, int full, float *out, int64_t out_ld,
                               void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned reflection filters.  The paper fits one non-negative reflection filter g per
+ * measured direction (Sec. III, Eq. 3 with G >= 0, Algorithm 1).  These calls run a small
+ * network that maps a direction to such a filter, so that directions between the measured
+ * ones get filters too (moving sources):
+ *     x  = (sin az, cos az, sin el, cos el, ear)         ear = -1 (left) or +1 (right)
+ *     h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), h3 = relu(W3 h2 + b3)     (256 wide)
+ *     g  = softplus(W4 h3 + b4)                           Lg taps, every one > 0
+ * trained by least squares on factorized reflection rows T (Algorithm 1 output):
+ *     L = 1/(2B) sum_b ||g_b - T_b||^2 over a batch of B rows,
+ * with Adam (Kingma & Ba 2015).  All arithmetic is FP32; all pointers are device memory.
+ *
+ * params  float [hrir_mlp_param_count(Lg)]: W1 [256][5], b1 [256], W2 [256][256], b2,
+ *         W3 [256][256], b3, W4 [Lg][256], b4 [Lg], concatenated, matrices row-major.
+ * dirs    float [n_rows][3]: {azimuth, elevation (radians), ear (-1 or +1)} per row.
+ * acts    float [n_rows][hrir_mlp_act_stride(Lg)]: the pre-activations of the four layers
+ *         (z1 | z2 | z3 | z4) that the backward pass needs.
+ *
+ * hrir_mlp_param_count  number of parameters (184520 for Lg = 200); 0 if Lg is out of range.
+ * hrir_mlp_act_stride   row stride of acts (floats).
+ * hrir_mlp_forward      out [n_rows][Lg] = g for every row; acts is filled when not NULL
+ *                       (otherwise the context workspace holds the activations in chunks).
+ * hrir_mlp_backward     grads [param_count] = dL/dparams for the batch whose forward pass left
+ *                       `acts` and `out`; target [n_rows][Lg]; loss (device float, may be
+ *                       NULL) = L.  1 <= n_rows <= 2^24.  Deterministic (fixed-order sums).
+ * hrir_mlp_adam         one Adam step t = step (>= 1) on n parameters: m and v are the first
+ *                       and second moments (zero before step 1), updated in place.
+ * Filters for rendering come from hrir_mlp_forward followed by hrir_topk_pack.
+ * ------------------------------------------------------------------------------------- */
+int64_t hrir_mlp_param_count(int refl_len);
+int64_t hrir_mlp_act_stride(int refl_len);
+int hrir_mlp_forward(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl_len,
+                     const float *params, float *out, float *acts, void *stream);
+int hrir_mlp_backward(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl_len,
+                      const float *params, const float *acts, const float *out,
+                      const float *target, float *grads, float *loss, void *stream);
+int hrir_mlp_adam(hrir_ctx *ctx, int64_t n, float *params, const float *grads, float *m,
+                  float *v, int step, float lr, float beta1, float beta2, float eps,
+                  void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Moving sources: Eqs. 1-2 with a direction per segment of seg_len samples.  Source s uses
+ * the reflection filter g_{s,j} in segment j (samples [j seg_len, (j+1) seg_len)); between
+ * segments the reflection output is cross-faded linearly in the output domain:
+ *     z[n] = (1 - a) (y * g_{s,j-1})[n] + a (y * g_{s,j})[n],  a = (n - j seg_len + 1) / seg_len,
+ * segment 0 uses g_{s,0} alone and outputs past the last segment use g_{s,n_seg-1} alone.
+ * The mix over sources is followed by the loaded resonance filter f (hrir_load_filters must
+ * have been called: f and Lg come from it); output as in hrir_render_batch.
+ *   src       device float [n_src][src_ld], 16-byte aligned, src_ld % 4 == 0.
+ *   tap_idx   device uint16 [n_src][n_seg][2][k_max] (indices < Lg, any order),
+ *   tap_w     device float  [n_src][n_seg][2][k_max], tap_nnz device uint8 [n_src][n_seg][2]
+ *             (the layout hrir_topk_pack writes for rows ordered (source, segment, ear)).
+ *             An index >= Lg or a count > k_max is ignored and flags HRIR_EINVAL for
+ *             hrir_sync.
+ *   seg_len   a multiple of 128;  1 <= k_max <= 255.
+ * ------------------------------------------------------------------------------------- */
+int hrir_render_moving(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, const float *src,
+                       int n_seg, int seg_len, int k_max, const uint16_t *tap_idx,
+                       const float *tap_w, const uint8_t *tap_nnz, int full, float *out,
+                       int64_t out_ld, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * The resonance stage applied per source, u_{s,e} = y_s * f_e (Sec. I footnote 2), the
+ * first half of Eq. 2 in the order (y * f) * g, which the paper notes can be precomputed
+ * when y is known in advance: u can then be rendered to any direction or trajectory with
+ * the reflection taps alone.  Computed on the tensor cores as a Toeplitz-block GEMM: every
+ * block of 32 outputs is one row of (Hankel window of y) x (Toeplitz matrix of f), with f
+ * split into three terms of the source's 16-bit type so that the FP32 accumulation gives
+ * y * f to about FP32 accuracy.  Uses the resonance of hrir_load_filters (Lf <= 32).
+ *   dt        HRIR_BF16 or HRIR_F16 (the sources' storage type).
+ *   src       device [n_src][src_ld] of dt, 16-byte aligned, src_ld % 8 == 0.
+ *   full      1: out_len = len + Lf - 1;  0: out_len = len.
+ *   out       device float [n_src][2][out_ld] (source s, ear e at out[(2 s + e) out_ld]),
+ *             16-byte aligned, out_ld >= out_len and out_ld % 4 == 0.
+ * ------------------------------------------------------------------------------------- */
+int hrir_resonance_per_source(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld,
+                              hrir_dtype dt, const void *src, int full, float *out,
+                              int64_t out_ld, void *stream);
 
 /* ---------------------------------------------------------------------------------------
  * Optional kernel timing, for benchmarks.  While enabled, the library brackets each of its
@@ -222,6 +302,9 @@ typedef enum {
     HRIR_K_REDUCE = 2,      /* fixed-order partial reduction + resonance FIR */
     HRIR_K_FFT = 3,         /* overlap-save FFT kernels */
     HRIR_K_TABLES = 4,      /* filter-pack kernels (top-K, records) */
+    HRIR_K_MLP = 5,         /* learned-filter network kernels (forward, backward, Adam) */
+    HRIR_K_MOVING = 6,      /* moving-source crossfade mixing kernel */
+    HRIR_K_RESONANCE = 7,   /* per-source resonance on the tensor cores */
     HRIR_K_COUNT = 8
 } hrir_kernel;
 

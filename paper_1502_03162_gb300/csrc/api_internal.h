@@ -39,6 +39,8 @@ struct hrir_ctx {
     size_t partial_bytes = 0;
     void *d_stage = nullptr;            // device staging for hrir_render_batch_host
     size_t stage_bytes = 0;
+    void *d_mlp_ws = nullptr;           // learned-filter network workspace
+    size_t mlp_ws_bytes = 0;
     int *d_status = nullptr;
 
     // optional kernel timing (hrir_set_timing)
@@ -58,6 +60,8 @@ namespace hrir_host {
 // Record a failure message on ctx (or the thread's create-error slot) and return code.
 int fail(hrir_ctx *ctx, int code, const char *fmt, ...);
 size_t dtype_size(int dt);
+// Make *ptr hold at least `need` bytes of device memory (grown with 1/8 slack).
+int grow(hrir_ctx *ctx, void **ptr, size_t *have, size_t need);
 int64_t round_up(int64_t x, int64_t m);
 // Pipeline depth (2..4) that fits the 227 KB shared-memory limit; 0 if none does.
 int pick_stages(int buf_elems, int elem_bytes, int rec_bytes, size_t *smem);

@@ -12,6 +12,7 @@ namespace hrir {
 enum : int {
     DEV_BAD_DIR = 1,    // a direction id was out of range (source rendered as silence)
     DEV_TIMEOUT = 2,    // a bounded mbarrier wait expired; the kernel returned early
+    DEV_BAD_TAP = 4,    // a device tap table held an index >= Lg or a count > k_max (ignored)
 };
 
 // Bounded waits give up after this many nanoseconds of %globaltimer.
@@ -57,6 +58,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Non-blocking test of phase `parity` (try_wait may suspend the thread for a while; this
+// never does).
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(bar), "r"(parity)

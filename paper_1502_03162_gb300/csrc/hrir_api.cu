@@ -280,6 +280,7 @@ void hrir_destroy(hrir_ctx *ctx)
     drop_timing_events(ctx);
     cudaFree(ctx->d_partial);
     cudaFree(ctx->d_stage);
+    cudaFree(ctx->d_mlp_ws);
     cudaFree(ctx->d_status);
     delete ctx;
 }
@@ -332,6 +333,8 @@ int hrir_sync(hrir_ctx *ctx, void *stream)
     CUDA_TRY(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
     if (st & DEV_TIMEOUT)
         return fail(ctx, HRIR_ETIMEDOUT, "a bounded device wait expired (output incomplete)");
+    if (st & DEV_BAD_TAP)
+        return fail(ctx, HRIR_EINVAL, "a device tap table held an index >= Lg or a count > k_max (ignored)");
     return fail(ctx, HRIR_EINVAL, "a direction id was out of range (rendered as silence)");
 }
 
@@ -396,7 +399,8 @@ int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k
     uint8_t *d_nnz = nullptr;
     const int sparse_nseg = (refl_len + kSparseSegment - 1) / kSparseSegment;
     const int sparse_nseg_pad = (int)round_up(sparse_nseg, 2);
-    const int sparse_rec = (int)round_up(16 + 8 * sparse_nseg_pad + 2 * (int64_t)k_max * 8, 16);
+    const int sparse_rec =
+        (int)round_up(16 + 8 * sparse_nseg_pad + 8 * (2 * (int64_t)k_max + 2 * sparse_nseg + 4), 16);
     const int dense_nchunk = (hrir_len + kDenseR - 1) / kDenseR;
     const int dense_padded = dense_nchunk * kDenseR;
     int rc = HRIR_OK;
@@ -546,6 +550,7 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
     a.table = sparse ? ctx->d_sparse : reinterpret_cast<const unsigned char *>(ctx->d_dense);
     a.rec_bytes = rec_bytes;
     a.nchunk = sparse ? ctx->sparse_nch_pad : nchunk;
+    a.nseg = sparse ? ctx->sparse_nchunk : 0;
     a.halo = halo;
     a.buf_elems = buf_elems;
     a.full_rows = (int)(len / kMixBox);

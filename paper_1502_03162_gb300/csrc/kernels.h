@@ -10,22 +10,24 @@
 namespace hrir {
 
 // ---- direct-convolution mixing (sparse reflection taps, or dense HRIR) -----------------
-// Outputs per lane (= window chunk width) and warps per CTA of each mixing kernel.  All warps
-// compute; warp 0 also issues the TMA loads.  The tile is warps x 32 lanes x R outputs.
+// Outputs per lane and warps per CTA of each mixing kernel.  Dense: all warps compute, warp 0
+// also issues the TMA loads, and the tile is warps x 32 lanes x R outputs.
 #ifndef HRIR_DENSE_R
 #define HRIR_DENSE_R 36
 #endif
 #ifndef HRIR_DENSE_WARPS
 #define HRIR_DENSE_WARPS 8
 #endif
-// Sparse kernel: windows in tensor memory, 8 warps x 32 lanes x 36 outputs (tile 9216); a
-// warp's TMEM row holds kSparseTmemCols samples = one segment of kSparseSegment filter
-// offsets plus the lane's outputs.
-constexpr int kSparseR = 36, kSparseWarps = 8;
+// Sparse kernel: windows in tensor memory.  4 TMEM lane quarters x 32 lanes x R = 52
+// consecutive outputs per lane (tile 6656); the two warps of a lane quarter (one per ear)
+// share a window of kSparseTmemCols samples = one segment of kSparseSegment filter offsets
+// plus the lane's outputs, double-buffered in the 512 TMEM columns; one more warp issues the
+// TMA loads.
+constexpr int kSparseR = 52, kSparseWarps = 8, kSparseQuarters = 4;
+constexpr int kSparseTile = kSparseQuarters * 32 * kSparseR;
 constexpr int kSparseTmemCols = 256;
-constexpr int kSparseSegment = kSparseTmemCols - kSparseR;  // 220
+constexpr int kSparseSegment = kSparseTmemCols - kSparseR;  // 204
 constexpr int kDenseR = HRIR_DENSE_R, kDenseWarps = HRIR_DENSE_WARPS;
-constexpr int kMixMaxR = 36;
 constexpr int kMixMaxStages = 4;
 constexpr int kMixBox = 256;                      // TMA box width (elements)
 constexpr int kRunSources = 64;                   // max sources per register accumulation run
@@ -43,6 +45,7 @@ struct MixArgs {
     int rec_bytes;              // record stride, multiple of 16
     int nchunk;                 // dense: filter span in chunks of R; sparse: length of the
                                 // per-segment count array of a record (even)
+    int nseg;                   // sparse: window segments per unit (records' segment count)
     int halo;                   // >= nchunk * R samples of history per tile (multiple of 8)
     int buf_elems;              // per-stage source buffer, multiple of kMixBox
     int full_rows;              // floor(len / kMixBox): rows of the 3-D source view
@@ -58,7 +61,6 @@ struct MixShape {
     int r, warps, tile;
 };
 MixShape mix_shape(int mode);
-size_t sparse_smem_bytes(int buf_elems, int elem_bytes, int rec_bytes, int stages);
 cudaError_t launch_sparse_tmem(int dtype, const CUtensorMap &tmap, const CUtensorMap &tmap3,
                                const MixArgs &a, int grid, size_t smem, cudaStream_t st);
 size_t mix_smem_bytes(int buf_elems, int elem_bytes, int rec_bytes, int stages);
@@ -122,6 +124,80 @@ cudaError_t launch_build_spectra(const float *dense, int padded_len, int hrir_le
 cudaError_t launch_fft_mix(int dtype, const CUtensorMap &tmap, const FftArgs &a, int grid,
                            size_t smem, cudaStream_t st);
 cudaError_t launch_fft_out(const FftOutArgs &a, int n_frames, cudaStream_t st);
+
+// ---- learned reflection filters: direction -> filter network (FP32) -----------------------
+constexpr int kMlpIn = 5;        // (sin az, cos az, sin el, cos el, ear)
+constexpr int kMlpHidden = 256;  // three hidden layers
+
+// C[m][n] = sum_k A(m, k) B(k, n), A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn];
+// the K range is split over blockIdx.z in chunks of k_chunk.  Epilogues (epi):
+// 0: Z = C + bias; 1: Z = C + bias and H = softplus(Z); 2: Z = C * [mask > 0];
+// 3: Z[z][m][n] = C (split-K partial, row stride ldz, M rows per split).
+struct GemmArgs {
+    int64_t M;
+    int N, K;
+    const float *A;
+    int64_t sam, sak;
+    const float *B;
+    int64_t sbk, sbn;
+    int k_chunk;
+    const float *bias;
+    float *Z;
+    int64_t ldz;
+    float *H;
+    int64_t ldh;
+    const float *mask;
+    int64_t ldm;
+};
+cudaError_t launch_gemm(int epi, bool relu_a, bool relu_b, const GemmArgs &g, int splits,
+                        cudaStream_t st);
+cudaError_t launch_features_layer1(int n_rows, const float *dirs, const float *W1, const float *b1,
+                                   float *z1, int64_t ldz, float *xs, cudaStream_t st);
+cudaError_t launch_output_grad(int64_t n_rows, int refl_len, const float *g, const float *tgt,
+                               const float *z4, int64_t ldz, float inv_b, float *dz, float *partial,
+                               int n_partial, float *loss, cudaStream_t st);
+cudaError_t launch_colsum(int64_t rows, int N, const float *D, int64_t ldd, float *out, cudaStream_t st);
+cudaError_t launch_split_reduce(int splits, int M, int N, const float *P, float *out, cudaStream_t st);
+cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v, float lr, float b1,
+                        float b2, float eps, float c1, float c2, cudaStream_t st);
+
+// ---- moving sources: per-segment filters with a linear crossfade ---------------------------
+constexpr int kMovTile = 1024;   // outputs per (tile, source) unit
+struct MovingArgs {
+    const float *src;            // [n_src][ld]
+    int64_t ld, len;
+    int n_src;
+    int n_seg, seg_len, k_max;   // tables [n_src][n_seg][2][k_max]
+    const uint16_t *tap_idx;
+    const float *tap_w;
+    const uint8_t *tap_nnz;      // [n_src][n_seg][2]
+    int refl_len;
+    int halo;                    // round_up(refl_len, 4)
+    int n_js;                    // segments staged per unit
+    Partition part;
+    float *partial;              // [n_tiles][slots][2][kMovTile]
+    int slots;
+    int *status;
+};
+size_t moving_smem_bytes(int halo, int n_js, int k_max);
+cudaError_t launch_moving_mix(const MovingArgs &a, int grid, size_t smem, cudaStream_t st);
+
+// ---- per-source resonance as a Toeplitz-block GEMM on the tensor cores ----------------------
+constexpr int kResTile = 4096;   // outputs per MMA tile (128 blocks of 32)
+constexpr int kResMaxLf = 32;    // resonance taps one block row covers
+struct ResonanceArgs {
+    int n_src;
+    int64_t out_len;             // samples of u per (source, ear)
+    const float *res;            // [2][res_len], res_len <= kResMaxLf
+    int res_len;
+    float *out;                  // [n_src][2][out_ld]
+    int64_t out_ld;
+    int *status;
+};
+size_t resonance_gemm_smem_bytes(int elem_bytes);
+// tmap: 2-D tensor map over the 16-bit sources with box {256, 1}
+cudaError_t launch_resonance_gemm(int dtype, const CUtensorMap &tmap, const ResonanceArgs &a,
+                                  int grid, cudaStream_t st);
 
 // ---- table builders and top-K -------------------------------------------------------------
 cudaError_t launch_topk(const float *g, int n_rows, int refl_len, int k, uint16_t *idx, float *w,

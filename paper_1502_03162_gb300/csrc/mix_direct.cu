@@ -278,7 +278,7 @@ size_t mix_smem_bytes(int buf_elems, int elem_bytes, int rec_bytes, int stages)
 
 MixShape mix_shape(int mode)
 {
-    if (mode == MIX_SPARSE) return {kSparseR, kSparseWarps, kSparseR * kSparseWarps * 32};
+    if (mode == MIX_SPARSE) return {kSparseR, kSparseWarps, kSparseTile};
     return {kDenseR, kDenseWarps, kDenseR * kDenseWarps * 32};
 }
 

@@ -5,17 +5,26 @@
 //
 // with each lane's source window held in tensor memory (TMEM).
 //
-// Each of the 8 warps owns 32 lanes x R = 36 consecutive outputs per lane (tile 9216).  For
-// every (source, tile) unit and every window segment of SW = 220 filter offsets, a lane
-// copies the 256 samples y[n - (seg+1) SW .. n - (seg+1) SW + 256) of its window from the
-// shared-memory source tile into its own TMEM row (256 columns; the warp's rows are its
-// TMEM lane quarter, warps w and w+4 use the two column halves).  A tap at offset o then
-// needs y[n + r - o] for r < R, which is the contiguous column range starting at
-// (seg+1) SW - o: one tcgen05.ld of 36 columns, warp-uniform address, no branch and no
-// register indexing, followed by 36 FMAs.  Left taps accumulate into one register set and
-// right taps into the other; the next tap's load is in flight while the current tap's FMAs
-// issue.  Staging (TMA), the persistent balanced work partition, run flushes into partial
-// slots and bounded waits are as in the dense mixing kernel.
+// A tile of 6656 outputs is split over the 4 TMEM lane quarters x 32 lanes, R = 52
+// consecutive outputs per lane.  The two warps of a lane quarter (warp q: left ear, warp
+// q + 4: right ear) share that quarter's TMEM rows.  For every (source, tile) unit and every
+// window segment of SW = 204 filter offsets, row (lane) holds the 256 samples
+// y[n - (seg+1) SW .. n - (seg+1) SW + 256) of its outputs' window.  A tap at offset o then
+// needs y[n + r - o] for r < R, the contiguous column range starting at (seg+1) SW - o: one
+// warp-uniform tcgen05.ld of 52 columns (no branch, no register indexing) followed by 52
+// FMAs; the next tap's load is in flight while the current tap's FMAs issue.
+//
+// The window is double-buffered in the 512 TMEM columns: while a pair of warps applies its
+// taps to one buffer, each warp copies half of the next window (shared memory -> registers
+// -> tcgen05.st) into the other, the left-ear warp before its taps and the right-ear warp
+// after them; a named barrier per pair (with
+// an AND vote, so that both warps leave together on a timeout) hands the buffers over.
+// Warp 0 also keeps a shared-memory ring filled with each unit's source tile (tensor TMA,
+// 256-sample halo, hardware zero fill outside [0, len)) and the direction's tap record
+// (bulk copy), issuing into stages as they free up without blocking unless the next window
+// needs the unit.  Work is a persistent balanced range of units per CTA; register accumulators are
+// flushed every <= 64 sources into partial slots that the reduction sums in a fixed order.
+// All waits are bounded.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -26,14 +35,21 @@ namespace hrir {
 namespace {
 
 constexpr int R = kSparseR;             // outputs per lane
-constexpr int NW = kSparseWarps;        // warps per CTA
-constexpr int kTile = NW * 32 * R;      // outputs per tile
-constexpr int kCols = kSparseTmemCols;  // TMEM columns per warp
+constexpr int NQ = kSparseQuarters;     // TMEM lane quarters
+constexpr int NW = kSparseWarps;        // warps: (lane quarter, ear); warp 0 also issues TMA
+constexpr int kTile = kSparseTile;      // outputs per tile
+constexpr int kCols = kSparseTmemCols;  // TMEM columns per window buffer
 constexpr int SW = kSparseSegment;      // filter offsets per window segment (= kCols - R)
-static_assert(SW + R == kCols, "window = segment + outputs per lane");
-static_assert(NW == 8 && kCols == 256, "two warps per TMEM lane quarter, 256 columns each");
+constexpr int kHalf = kCols / 2;        // window columns each warp of a pair copies
+constexpr int kCopyChunks = kHalf / 32; // tcgen05.st.x32 per warp per window
+static_assert(NW == 2 * NQ, "one warp per (lane quarter, ear)");
+static_assert(SW + R == kCols && 2 * kCols == 512, "two window buffers fill the 512 columns");
+static_assert(R % 4 == 0 && ((R / 4) & 1), "lane stride must be an odd number of 16-byte groups");
+static_assert(R == 32 + 16 + 4, "a slice is loaded as x32 + x16 + x4 columns");
+static_assert(kTile % kMixBox == 0, "tiles start on a row of the 3-D source view");
 
-// ---- 32 consecutive samples, widened to FP32 (conflict-free: lane stride R = 36 elements) --
+// ---- 32 consecutive samples, widened to FP32 (conflict-free: the lane stride R is an odd
+// number of 16-byte groups) ------------------------------------------------------------------
 template <typename T>
 struct Load32;
 
@@ -104,8 +120,8 @@ __device__ __forceinline__ void tm_st32(uint32_t taddr, const uint32_t (&v)[32])
 
 __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// R = 36 columns starting at taddr into v (async; valid after tm_wait_ld(v))
-__device__ __forceinline__ void tm_ld36(uint32_t taddr, uint32_t (&v)[R])
+// R = 52 columns starting at taddr into v (async; valid after tm_wait_ld(v))
+__device__ __forceinline__ void tm_ld(uint32_t taddr, uint32_t (&v)[R])
 {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
@@ -118,26 +134,56 @@ __device__ __forceinline__ void tm_ld36(uint32_t taddr, uint32_t (&v)[R])
           "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
         : "r"(taddr)
         : "memory");
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];"
+        : "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]),
+          "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]),
+          "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47])
+        : "r"(taddr + 32)
+        : "memory");
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35])
-                 : "r"(taddr + 32)
+                 : "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51])
+                 : "r"(taddr + 48)
                  : "memory");
 }
 
-// Wait for this thread's outstanding tcgen05.ld; v is threaded through so that no use of
-// the loaded registers can be scheduled before the wait.
-__device__ __forceinline__ void tm_wait_ld(uint32_t (&v)[R])
+// Wait for this thread's outstanding tcgen05.ld.  v and acc are threaded through the
+// statements (volatile statements keep their order), so no use of the loaded registers moves
+// above the wait and every FMA into acc issued before it stays before it: the FMAs of
+// consecutive taps are never interleaved on the same accumulator.
+__device__ __forceinline__ void tm_wait_ld(uint32_t (&v)[R], float (&acc)[R])
 {
-    asm volatile(
-        "tcgen05.wait::ld.sync.aligned;"
-        : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
-          "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]),
-          "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]),
-          "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]),
-          "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31]),
-          "+r"(v[32]), "+r"(v[33]), "+r"(v[34]), "+r"(v[35])
-        :
-        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25])
+                 :
+                 : "memory");
+    asm volatile(""
+                 : "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31]), "+r"(v[32]), "+r"(v[33]), "+r"(v[34]), "+r"(v[35]), "+r"(v[36]), "+r"(v[37]), "+r"(v[38]), "+r"(v[39]), "+r"(v[40]), "+r"(v[41]), "+r"(v[42]), "+r"(v[43]), "+r"(v[44]), "+r"(v[45]), "+r"(v[46]), "+r"(v[47]), "+r"(v[48]), "+r"(v[49]), "+r"(v[50]), "+r"(v[51])
+                 :
+                 : "memory");
+    asm volatile(""
+                 : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]), "+f"(acc[6]), "+f"(acc[7]), "+f"(acc[8]), "+f"(acc[9]), "+f"(acc[10]), "+f"(acc[11]), "+f"(acc[12]), "+f"(acc[13]), "+f"(acc[14]), "+f"(acc[15]), "+f"(acc[16]), "+f"(acc[17]), "+f"(acc[18]), "+f"(acc[19]), "+f"(acc[20]), "+f"(acc[21]), "+f"(acc[22]), "+f"(acc[23]), "+f"(acc[24]), "+f"(acc[25])
+                 :
+                 : "memory");
+    asm volatile(""
+                 : "+f"(acc[26]), "+f"(acc[27]), "+f"(acc[28]), "+f"(acc[29]), "+f"(acc[30]), "+f"(acc[31]), "+f"(acc[32]), "+f"(acc[33]), "+f"(acc[34]), "+f"(acc[35]), "+f"(acc[36]), "+f"(acc[37]), "+f"(acc[38]), "+f"(acc[39]), "+f"(acc[40]), "+f"(acc[41]), "+f"(acc[42]), "+f"(acc[43]), "+f"(acc[44]), "+f"(acc[45]), "+f"(acc[46]), "+f"(acc[47]), "+f"(acc[48]), "+f"(acc[49]), "+f"(acc[50]), "+f"(acc[51])
+                 :
+                 : "memory");
+}
+
+// Keep every FMA into acc after this point (issued after a TMEM load, so that the load is
+// in flight while they run).
+__device__ __forceinline__ void tie_acc(float (&acc)[R])
+{
+    asm volatile(""
+                 : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]), "+f"(acc[6]), "+f"(acc[7]), "+f"(acc[8]), "+f"(acc[9]), "+f"(acc[10]), "+f"(acc[11]), "+f"(acc[12]), "+f"(acc[13]), "+f"(acc[14]), "+f"(acc[15]), "+f"(acc[16]), "+f"(acc[17]), "+f"(acc[18]), "+f"(acc[19]), "+f"(acc[20]), "+f"(acc[21]), "+f"(acc[22]), "+f"(acc[23]), "+f"(acc[24]), "+f"(acc[25])
+                 :
+                 : "memory");
+    asm volatile(""
+                 : "+f"(acc[26]), "+f"(acc[27]), "+f"(acc[28]), "+f"(acc[29]), "+f"(acc[30]), "+f"(acc[31]), "+f"(acc[32]), "+f"(acc[33]), "+f"(acc[34]), "+f"(acc[35]), "+f"(acc[36]), "+f"(acc[37]), "+f"(acc[38]), "+f"(acc[39]), "+f"(acc[40]), "+f"(acc[41]), "+f"(acc[42]), "+f"(acc[43]), "+f"(acc[44]), "+f"(acc[45]), "+f"(acc[46]), "+f"(acc[47]), "+f"(acc[48]), "+f"(acc[49]), "+f"(acc[50]), "+f"(acc[51])
+                 :
+                 : "memory");
 }
 
 __device__ __forceinline__ void fma_slice(float (&acc)[R], const uint32_t (&v)[R], float w)
@@ -146,42 +192,61 @@ __device__ __forceinline__ void fma_slice(float (&acc)[R], const uint32_t (&v)[R
     for (int r = 0; r < R; ++r) acc[r] = fmaf(w, __uint_as_float(v[r]), acc[r]);
 }
 
-// Apply n taps {column, weight bits} to acc.  TMEM loads are double-buffered (the next
-// tap's slice is in flight while the current tap's FMAs issue) and tap records are read
-// from shared memory two taps ahead, so no load feeds an address right away.
+// Barrier of the two warps of lane quarter q (named barrier 1 + q, 64 threads) that also
+// returns the AND of `ok` over them; TMEM accesses before it are ordered before those after.
+__device__ __forceinline__ bool pair_sync_all(int q, bool ok)
+{
+    uint32_t r;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    asm volatile(
+        "{\n\t.reg .pred p, v;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred v, %2, 64, p;\n\t"
+        "selp.u32 %0, 1, 0, v;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)ok), "r"(1 + q)
+        : "memory");
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return r != 0;
+}
+
+// This warp's half of a window (kHalf columns of its 32 TMEM lanes): shared memory ->
+// registers -> tcgen05.st, all loads issued before the first store.
+template <typename T>
+__device__ __forceinline__ void copy_half(const T *src, uint32_t dst)
+{
+    uint32_t v[kCopyChunks][32];
+#pragma unroll
+    for (int c = 0; c < kCopyChunks; ++c) Load32<T>::run(src + 32 * c, v[c]);
+#pragma unroll
+    for (int c = 0; c < kCopyChunks; ++c) tm_st32(dst + 32 * c, v[c]);
+}
+
+// Apply n taps {column, weight bits} of this warp's ear to acc (n even: the lists are padded
+// with zero-weight taps, and at least 4 readable entries follow each list).  TMEM loads are
+// double-buffered: the next tap's slice is in flight while the current tap's FMAs issue.
 __device__ __forceinline__ void apply_taps(float (&acc)[R], uint32_t tw, const int2 *taps, int n)
 {
     if (n <= 0) return;
     uint32_t A[R], B[R];
-    int2 cur = taps[0];
-    int2 nxt = n > 1 ? taps[1] : cur;
-    tm_ld36(tw + (uint32_t)cur.x, A);
-    int2 nn = n > 2 ? taps[2] : cur;
-    tm_wait_ld(A);
-    int t = 0;
-    while (true) {
-        bool more = t + 1 < n;
-        if (more) tm_ld36(tw + (uint32_t)nxt.x, B);
-        fma_slice(acc, A, __int_as_float(cur.y));
-        if (!more) break;
-        cur = nxt;
-        nxt = nn;
-        nn = t + 3 < n ? taps[t + 3] : cur;
-        tm_wait_ld(B);
-        ++t;
-        more = t + 1 < n;
-        if (more) tm_ld36(tw + (uint32_t)nxt.x, A);
-        fma_slice(acc, B, __int_as_float(cur.y));
-        if (!more) break;
-        cur = nxt;
-        nxt = nn;
-        nn = t + 3 < n ? taps[t + 3] : cur;
-        tm_wait_ld(A);
-        ++t;
+    int2 t0 = taps[0], t1 = taps[1];
+    tm_ld(tw + (uint32_t)t0.x, A);
+    for (int i = 0; i < n; i += 2) {
+        const int2 t2 = taps[i + 2], t3 = taps[i + 3];
+        tm_wait_ld(A, acc);
+        tm_ld(tw + (uint32_t)t1.x, B);
+        tie_acc(acc);
+        fma_slice(acc, A, __int_as_float(t0.y));
+        tm_wait_ld(B, acc);
+        if (i + 2 < n) tm_ld(tw + (uint32_t)t2.x, A);
+        tie_acc(acc);
+        fma_slice(acc, B, __int_as_float(t1.y));
+        t0 = t2;
+        t1 = t3;
     }
 }
 
-// Issue the TMA loads of unit u into a pipeline stage (all lanes of warp 0).
+// Issue the TMA loads of unit u into a pipeline stage (all lanes of the producer warp).
 template <typename T>
 __device__ __forceinline__ void issue_unit(const CUtensorMap *tmap, const CUtensorMap *tmap3,
                                            const MixArgs &a, int64_t u, int d, T *ybuf,
@@ -209,7 +274,7 @@ __device__ __forceinline__ void issue_unit(const CUtensorMap *tmap, const CUtens
                     full_bar);
 }
 
-// Raw direction id of unit u (the load stays in flight until checked_dir uses it).
+// Raw direction id of unit u.
 __device__ __forceinline__ int raw_dir(const MixArgs &a, int64_t u)
 {
     return __ldg(a.dir + (int)(u % a.n_src));
@@ -225,8 +290,9 @@ __device__ __forceinline__ int checked_dir(const MixArgs &a, int d, int lane)
     return d;
 }
 
-// Record: int4 {n_seg, 0, 0, 0}, int2 cnt[nch_pad] {n_left, n_right} per segment, then per
-// segment its left taps and right taps as int2 {TMEM column, weight bits}.
+// Record: int4 {n_seg, 0, 0, 0}, int2 cnt[nchunk] {n_left, n_right} per segment, then per
+// segment its left taps and right taps as int2 {window column, weight bits}, each list padded
+// to an even length with zero-weight taps, and 4 padding entries at the end.
 template <typename T>
 __global__ void __launch_bounds__(NW * 32, 1)
     sparse_tmem_kernel(const __grid_constant__ CUtensorMap tmap,
@@ -245,8 +311,8 @@ __global__ void __launch_bounds__(NW * 32, 1)
         prefetch_tensormap(&tmap);
         prefetch_tensormap(&tmap3);
         for (int i = 0; i < stages; ++i) {
-            mbar_init(smem_addr(&bars[i]), 1);
-            mbar_init(smem_addr(&bars[stages + i]), NW);
+            mbar_init(smem_addr(&bars[i]), 1);              // full: producer + tx bytes
+            mbar_init(smem_addr(&bars[stages + i]), NW);    // empty: one arrive per warp
         }
         *abort_flag = 0;
         mbar_fence_init();
@@ -261,97 +327,128 @@ __global__ void __launch_bounds__(NW * 32, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem_base = *tmem_slot;
-    // this warp: TMEM lanes 32*(warp%4).., columns 256*(warp/4)..
-    const uint32_t tw = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(kCols * (warp >> 2));
 
     const int64_t u_begin = a.part.first(blockIdx.x);
     const int64_t u_end = a.part.first(blockIdx.x + 1);
     const int64_t n_units = u_end - u_begin;
+    int64_t issued = 0;  // units issued (warp 0)
+    int next_dir = n_units > 0 ? raw_dir(a, u_begin) : 0;  // direction of unit `issued`, in flight
 
-    int next_dir = 0;
-    int64_t issued = 0;
-    if (warp == 0) {
-        const int64_t n0 = n_units < stages ? n_units : stages;
-        for (int64_t i = 0; i < n0; ++i) {
-            const int d = checked_dir(a, raw_dir(a, u_begin + i), lane);
-            issue_unit<T>(&tmap, &tmap3, a, u_begin + i, d, ybuf + (size_t)i * a.buf_elems,
-                          rbuf + (size_t)i * a.rec_bytes, smem_addr(&bars[i]), lane);
-        }
-        issued = n0;
-        if (issued < n_units) next_dir = raw_dir(a, u_begin + issued);
-    }
-
-    const int lane_off = (warp * 32 + lane) * R;
-    float accL[R], accR[R];
-#pragma unroll
-    for (int i = 0; i < R; ++i) accL[i] = accR[i] = 0.f;
-    int cur_t = -1, slot = 0, run_n = 0;
-    int64_t k = 0;
-    for (; k < n_units; ++k) {
-        const int64_t u = u_begin + k;
-        if (warp == 0 && k >= 1 && issued < n_units) {
-            const int st = (int)((k - 1) % stages);
-            const uint32_t par = (uint32_t)(((k - 1) / stages) & 1);
-            if (!mbar_wait_bounded(smem_addr(&bars[stages + st]), par, abort_flag, a.status)) break;
-            issue_unit<T>(&tmap, &tmap3, a, u_begin + issued, checked_dir(a, next_dir, lane),
-                          ybuf + (size_t)st * a.buf_elems, rbuf + (size_t)st * a.rec_bytes,
-                          smem_addr(&bars[st]), lane);
+    // Warp 0: issue units into free stages; those up to `must` are waited for (bounded), the
+    // rest only if their stage is already free.  Returns false on a timeout.
+    auto fill = [&](int64_t must) {
+        while (issued < n_units) {
+            const int st = (int)(issued % stages);
+            if (issued >= stages) {
+                const uint32_t eb = smem_addr(&bars[stages + st]);
+                const uint32_t par = (uint32_t)((issued / stages - 1) & 1);
+                if (issued <= must) {
+                    if (!mbar_wait_bounded(eb, par, abort_flag, a.status)) return false;
+                } else if (!mbar_test_wait(eb, par)) {
+                    break;
+                }
+            }
+            const int d = checked_dir(a, next_dir, lane);
+            issue_unit<T>(&tmap, &tmap3, a, u_begin + issued, d, ybuf + (size_t)st * a.buf_elems,
+                          rbuf + (size_t)st * a.rec_bytes, smem_addr(&bars[st]), lane);
             ++issued;
             if (issued < n_units) next_dir = raw_dir(a, u_begin + issued);
         }
-        const int t = (int)(u / a.n_src);
-        if (t != cur_t) {
-            cur_t = t;
-            slot = a.part.slot_base(blockIdx.x, t);
-            run_n = 0;
-        }
-        const int st = (int)(k % stages);
-        if (!mbar_wait_bounded(smem_addr(&bars[st]), (uint32_t)((k / stages) & 1), abort_flag,
-                               a.status))
-            break;
-        const T *yb = ybuf + (size_t)st * a.buf_elems;
-        const unsigned char *rec = rbuf + (size_t)st * a.rec_bytes;
-        const int n_seg = *reinterpret_cast<const int *>(rec);
-        const int2 *cnt = reinterpret_cast<const int2 *>(rec + 16);
-        const int2 *taps = reinterpret_cast<const int2 *>(rec + 16 + 8 * a.nchunk);
-        for (int seg = 0; seg < n_seg; ++seg) {
-            const int2 c = cnt[seg];
-            if (c.x + c.y == 0) continue;
-            // window of this lane: y[n - (seg+1) SW + j], j < kCols, into its TMEM row
-            const T *src = yb + a.halo + lane_off - (seg + 1) * SW;
-#pragma unroll 1
-            for (int q = 0; q < kCols / 32; ++q) {
-                uint32_t v[32];
-                Load32<T>::run(src + 32 * q, v);
-                tm_st32(tw + 32 * q, v);
+        return true;
+    };
+
+    if (n_units > 0) {
+        // ---- compute: warp (q, ear) ----
+        const int q = warp & (NQ - 1), ear = warp / NQ;
+        const uint32_t tq = tmem_base + ((uint32_t)(32 * q) << 16);
+        const int lane_off = (q * 32 + lane) * R;
+        const int n_seg = a.nseg;
+        const int64_t n_steps = n_units * n_seg;
+        float acc[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) acc[i] = 0.f;
+        int cur_t = -1, slot = 0, run_n = 0;
+
+        // the window of a step (unit k, segment s) for this warp's half
+        auto window_src = [&](int64_t k, int s) {
+            return ybuf + (size_t)(k % stages) * a.buf_elems + a.halo + lane_off - (s + 1) * SW +
+                   kHalf * ear;
+        };
+        // prologue: fill the ring, the first window into buffer 0
+        bool ok = warp == 0 ? fill(0) : true;
+        ok = ok && mbar_wait_bounded(smem_addr(&bars[0]), 0u, abort_flag, a.status);
+        if (ok) copy_half<T>(window_src(0, 0), tq + (uint32_t)(kHalf * ear));
+        tm_wait_st();
+        ok = pair_sync_all(q, ok);
+
+        int64_t k = 0;
+        int s = 0, toff = 0;
+        for (int64_t j = 0; ok && j < n_steps; ++j) {
+            int64_t k1 = k;
+            int s1 = s + 1;
+            if (s1 == n_seg) {
+                s1 = 0;
+                k1 = k + 1;
             }
+            const bool have_next = k1 < n_units;
+            bool ok_next = warp == 0 ? fill(k1) : true;
+            if (ok_next && have_next && s1 == 0)
+                ok_next = mbar_wait_bounded(smem_addr(&bars[k1 % stages]),
+                                            (uint32_t)((k1 / stages) & 1), abort_flag, a.status);
+            // the next window's half: the left-ear warp copies it before its taps, the
+            // right-ear warp after them, so that on their shared SM sub-partition one warp's
+            // copy overlaps the other's FMAs
+            const bool copy = have_next && ok_next;
+            const T *nsrc = window_src(copy ? k1 : k, copy ? s1 : s);
+            const uint32_t ndst = tq + (uint32_t)(kCols * ((j + 1) & 1) + kHalf * ear);
+            if (copy && ear == 0) copy_half<T>(nsrc, ndst);
+            // taps of this warp's ear in segment s of unit k
+            const unsigned char *rec = rbuf + (size_t)(k % stages) * a.rec_bytes;
+            const int2 c = reinterpret_cast<const int2 *>(rec + 16)[s];
+            const int2 *taps = reinterpret_cast<const int2 *>(rec + 16 + 8 * a.nchunk) + toff +
+                               (ear ? c.x : 0);
+            apply_taps(acc, tq + (uint32_t)(kCols * (j & 1)), taps, ear ? c.y : c.x);
+            toff += c.x + c.y;
+            if (copy && ear == 1) copy_half<T>(nsrc, ndst);
             tm_wait_st();
-            apply_taps(accL, tw, taps, c.x);
-            apply_taps(accR, tw, taps + c.x, c.y);
-            taps += c.x + c.y;
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_addr(&bars[stages + st]));
-        ++run_n;
-        const bool tile_end = (u + 1 == u_end) || ((u + 1) / a.n_src != t);
-        if (run_n == a.part.gs || tile_end) {
-            float *p = a.partial + ((size_t)t * a.slots + slot) * 2 * kTile + lane_off;
-            float4 *pl = reinterpret_cast<float4 *>(p);
-            float4 *pr = reinterpret_cast<float4 *>(p + kTile);
+            ok = pair_sync_all(q, ok_next);
+            if (s == n_seg - 1) {
+                // unit k done: release its stage, flush the run at its end
+                const int64_t u = u_begin + k;
+                const int t = (int)(u / a.n_src);
+                if (t != cur_t) {
+                    cur_t = t;
+                    slot = a.part.slot_base(blockIdx.x, t);
+                    run_n = 0;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&bars[stages + (int)(k % stages)]));
+                ++run_n;
+                const bool tile_end = (u + 1 == u_end) || ((u + 1) / a.n_src != t);
+                if (run_n == a.part.gs || tile_end) {
+                    float4 *p = reinterpret_cast<float4 *>(
+                        a.partial + ((size_t)t * a.slots + slot) * 2 * kTile + ear * kTile + lane_off);
 #pragma unroll
-            for (int i = 0; i < R / 4; ++i) {
-                pl[i] = make_float4(accL[4 * i], accL[4 * i + 1], accL[4 * i + 2], accL[4 * i + 3]);
-                pr[i] = make_float4(accR[4 * i], accR[4 * i + 1], accR[4 * i + 2], accR[4 * i + 3]);
+                    for (int i = 0; i < R / 4; ++i)
+                        p[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+#pragma unroll
+                    for (int i = 0; i < R; ++i) acc[i] = 0.f;
+                    ++slot;
+                    run_n = 0;
+                }
+                toff = 0;
             }
-#pragma unroll
-            for (int i = 0; i < R; ++i) accL[i] = accR[i] = 0.f;
-            ++slot;
-            run_n = 0;
+            k = k1;
+            s = s1;
         }
     }
-    if (warp == 0 && k < n_units) {
-        // aborted: let the copies still in flight land (bounded)
-        for (int64_t j = k; j < issued; ++j) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) {
+        // let every copy still in flight land before the CTA exits (bounded; immediate unless
+        // a wait timed out)
+        for (int64_t j = issued > stages ? issued - stages : 0; j < issued; ++j) {
             const uint32_t fb = smem_addr(&bars[j % stages]);
             const uint32_t par = (uint32_t)((j / stages) & 1);
             const uint64_t t0 = global_timer_ns();
@@ -359,19 +456,11 @@ __global__ void __launch_bounds__(NW * 32, 1)
             }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
 }
 
 }  // namespace
-
-size_t sparse_smem_bytes(int buf_elems, int elem_bytes, int rec_bytes, int stages)
-{
-    return (size_t)stages * ((size_t)buf_elems * elem_bytes + rec_bytes) + 2 * stages * 8 + 16;
-}
 
 template <typename T>
 static cudaError_t launch_t(const CUtensorMap &tmap, const CUtensorMap &tmap3, const MixArgs &a,

@@ -1,0 +1,313 @@
+// mlp.cu -- learned reflection filters: the direction -> filter network (5 -> 256 -> 256 ->
+// 256 -> Lg, ReLU, softplus output so every tap is >= 0 like the paper's G >= 0, Eq. 3),
+// its backward pass for the least-squares loss against factorized reflection rows
+// (Algorithm 1 output), and the Adam update.  All FP32.
+//
+//  * features_layer1_kernel: x = (sin az, cos az, sin el, cos el, ear) per row, and
+//    z1 = W1 x + b1 (K = 5: one thread per output column, rows staged in shared memory).
+//  * gemm_kernel: C[m][n] = sum_k A(m, k) B(k, n) over arbitrary strides (so the forward
+//    X W^T, the backward dZ W and the weight gradient dZ^T X are one kernel), 64 x 64 tile,
+//    k-step 16, 4 x 4 outputs per thread, optional ReLU on the A or B operand as it is
+//    loaded (layers keep pre-activations z; h = relu(z) is formed on load), and fused
+//    epilogues: + bias (and softplus into a second output), x [mask > 0] (ReLU'), or a
+//    split-K partial that a second kernel sums in a fixed order (deterministic).
+//  * output_grad_kernel: dz4 = (g - t) / B * sigmoid(z4) and per-block loss partials.
+//  * colsum_kernel: bias gradients, fixed-order column sums.
+//  * adam_kernel: the Adam update with host-computed bias corrections.
+#include "kernels.h"
+
+namespace hrir {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+enum Epi : int { EPI_BIAS = 0, EPI_BIAS_SOFTPLUS = 1, EPI_MASK = 2, EPI_PARTIAL = 3 };
+
+__device__ __forceinline__ float softplus_f(float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); }
+
+__device__ __forceinline__ float sigmoid_f(float z)
+{
+    const float e = expf(-fabsf(z));
+    return z >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
+}
+
+template <int EPI, bool RELU_A, bool RELU_B>
+__global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs g)
+{
+    __shared__ float As[BK][BM + 4];
+    __shared__ float Bs[BK][BN + 4];
+    const int64_t m0 = (int64_t)blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    const int kb = blockIdx.z * g.k_chunk;
+    const int ke = min(g.K, kb + g.k_chunk);
+    const int t = threadIdx.x;
+    const int tm = (t >> 4) * 4, tn = (t & 15) * 4;
+    float c[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) c[i][j] = 0.f;
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = t + 256 * i;
+            int kk, mm;
+            if (g.sak == 1) {
+                kk = e & (BK - 1);
+                mm = e >> 4;
+            } else {
+                mm = e & (BM - 1);
+                kk = e >> 6;
+            }
+            const int64_t m = m0 + mm;
+            const int k = k0 + kk;
+            float v = (m < g.M && k < ke) ? g.A[m * g.sam + (int64_t)k * g.sak] : 0.f;
+            if (RELU_A) v = fmaxf(v, 0.f);
+            As[kk][mm] = v;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = t + 256 * i;
+            int kk, nn;
+            if (g.sbn == 1) {
+                nn = e & (BN - 1);
+                kk = e >> 6;
+            } else {
+                kk = e & (BK - 1);
+                nn = e >> 4;
+            }
+            const int n = n0 + nn;
+            const int k = k0 + kk;
+            float v = (n < g.N && k < ke) ? g.B[(int64_t)k * g.sbk + (int64_t)n * g.sbn] : 0.f;
+            if (RELU_B) v = fmaxf(v, 0.f);
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i] = As[kk][tm + i];
+                b[i] = Bs[kk][tn + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) c[i][j] = fmaf(a[i], b[j], c[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t m = m0 + tm + i;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tn + j;
+            if (n >= g.N) continue;
+            float v = c[i][j];
+            if (EPI == EPI_BIAS || EPI == EPI_BIAS_SOFTPLUS) {
+                v += g.bias[n];
+                g.Z[m * g.ldz + n] = v;
+                if (EPI == EPI_BIAS_SOFTPLUS) g.H[m * g.ldh + n] = softplus_f(v);
+            } else if (EPI == EPI_MASK) {
+                g.Z[m * g.ldz + n] = g.mask[m * g.ldm + n] > 0.f ? v : 0.f;
+            } else {
+                g.Z[((int64_t)blockIdx.z * g.M + m) * g.ldz + n] = v;
+            }
+        }
+    }
+}
+
+// z1[b][n] = b1[n] + sum_k W1[n][k] x_b[k] (skipped when z1 == nullptr); also writes x_b
+// (5 features, row stride 8) to xs when xs != nullptr.  Rows: {az, el, ear} with ear = -1 (left) or +1 (right).
+constexpr int kL1Rows = 16;
+__global__ void __launch_bounds__(256) features_layer1_kernel(int n_rows, const float *__restrict__ dirs,
+                                                              const float *__restrict__ W1,
+                                                              const float *__restrict__ b1,
+                                                              float *__restrict__ z1, int64_t ldz,
+                                                              float *__restrict__ xs)
+{
+    __shared__ float x[kL1Rows][kMlpIn];
+    const int64_t r0 = (int64_t)blockIdx.x * kL1Rows;
+    const int t = threadIdx.x;
+    if (t < kL1Rows && r0 + t < n_rows) {
+        const float *d = dirs + (r0 + t) * 3;
+        float sa, ca, se, ce;
+        sincosf(d[0], &sa, &ca);
+        sincosf(d[1], &se, &ce);
+        x[t][0] = sa;
+        x[t][1] = ca;
+        x[t][2] = se;
+        x[t][3] = ce;
+        x[t][4] = d[2];
+        if (xs) {
+            float *o = xs + (r0 + t) * 8;
+            for (int k = 0; k < kMlpIn; ++k) o[k] = x[t][k];
+            for (int k = kMlpIn; k < 8; ++k) o[k] = 0.f;
+        }
+    }
+    __syncthreads();
+    if (!z1) return;
+    for (int n = t; n < kMlpHidden; n += blockDim.x) {
+        float w[kMlpIn];
+#pragma unroll
+        for (int k = 0; k < kMlpIn; ++k) w[k] = W1[n * kMlpIn + k];
+        const float bias = b1[n];
+        for (int r = 0; r < kL1Rows && r0 + r < n_rows; ++r) {
+            float v = bias;
+#pragma unroll
+            for (int k = 0; k < kMlpIn; ++k) v = fmaf(w[k], x[r][k], v);
+            z1[(r0 + r) * ldz + n] = v;
+        }
+    }
+}
+
+// dz[b][j] = (g[b][j] - t[b][j]) * inv_b * sigmoid(z4[b][j]); partial[block] = sum (g - t)^2
+__global__ void __launch_bounds__(256) output_grad_kernel(int64_t n_rows, int refl_len,
+                                                          const float *__restrict__ g,
+                                                          const float *__restrict__ tgt,
+                                                          const float *__restrict__ z4, int64_t ldz,
+                                                          float inv_b, float *__restrict__ dz,
+                                                          float *__restrict__ partial)
+{
+    __shared__ float red[256];
+    const int64_t total = n_rows * refl_len;
+    float s = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / refl_len;
+        const int j = (int)(i - b * refl_len);
+        const float d = g[i] - tgt[i];
+        s = fmaf(d, d, s);
+        dz[i] = d * inv_b * sigmoid_f(z4[b * ldz + j]);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// loss = 0.5 * inv_b * sum partial (fixed order)
+__global__ void loss_final_kernel(const float *__restrict__ partial, int n, float inv_b,
+                                  float *__restrict__ loss)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += partial[i];
+        *loss = (float)(0.5 * inv_b * s);
+    }
+}
+
+// out[n] = sum_b D[b][n] (b in order) for n < N
+__global__ void colsum_kernel(int64_t rows, int N, const float *__restrict__ D, int64_t ldd,
+                              float *__restrict__ out)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.f;
+    for (int64_t b = 0; b < rows; ++b) s += D[b * ldd + n];
+    out[n] = s;
+}
+
+// out[m][n] = sum_z P[z][m][n] (z in order)
+__global__ void split_reduce_kernel(int splits, int M, int N, const float *__restrict__ P,
+                                    float *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t MN = (int64_t)M * N;
+    if (i >= MN) return;
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += P[z * MN + i];
+    out[i] = s;
+}
+
+__global__ void adam_kernel(int64_t n, float *__restrict__ p, const float *__restrict__ g,
+                            float *__restrict__ m, float *__restrict__ v, float lr, float b1,
+                            float b2, float eps, float c1, float c2)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+template <int EPI, bool RA, bool RB>
+cudaError_t gemm_t(const GemmArgs &g, int splits, cudaStream_t st)
+{
+    dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN), (unsigned)splits);
+    gemm_kernel<EPI, RA, RB><<<grid, 256, 0, st>>>(g);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_gemm(int epi, bool relu_a, bool relu_b, const GemmArgs &g, int splits,
+                        cudaStream_t st)
+{
+    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    if ((g.M + BM - 1) / BM > 0x7fffffff || splits < 1) return cudaErrorInvalidValue;
+#define HRIR_GEMM_CASE(E, A, B)                                                     \
+    if (epi == E && relu_a == A && relu_b == B) return gemm_t<E, A, B>(g, splits, st);
+    HRIR_GEMM_CASE(EPI_BIAS, true, false)
+    HRIR_GEMM_CASE(EPI_BIAS_SOFTPLUS, true, false)
+    HRIR_GEMM_CASE(EPI_MASK, false, false)
+    HRIR_GEMM_CASE(EPI_PARTIAL, false, true)
+    HRIR_GEMM_CASE(EPI_PARTIAL, false, false)
+#undef HRIR_GEMM_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_features_layer1(int n_rows, const float *dirs, const float *W1, const float *b1,
+                                   float *z1, int64_t ldz, float *xs, cudaStream_t st)
+{
+    if (n_rows <= 0) return cudaSuccess;
+    features_layer1_kernel<<<(n_rows + kL1Rows - 1) / kL1Rows, 256, 0, st>>>(n_rows, dirs, W1, b1, z1,
+                                                                              ldz, xs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_output_grad(int64_t n_rows, int refl_len, const float *g, const float *tgt,
+                               const float *z4, int64_t ldz, float inv_b, float *dz, float *partial,
+                               int n_partial, float *loss, cudaStream_t st)
+{
+    output_grad_kernel<<<n_partial, 256, 0, st>>>(n_rows, refl_len, g, tgt, z4, ldz, inv_b, dz, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !loss) return e;
+    loss_final_kernel<<<1, 32, 0, st>>>(partial, n_partial, inv_b, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colsum(int64_t rows, int N, const float *D, int64_t ldd, float *out, cudaStream_t st)
+{
+    colsum_kernel<<<(N + 127) / 128, 128, 0, st>>>(rows, N, D, ldd, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_reduce(int splits, int M, int N, const float *P, float *out, cudaStream_t st)
+{
+    const int64_t MN = (int64_t)M * N;
+    split_reduce_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(splits, M, N, P, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v, float lr, float b1,
+                        float b2, float eps, float c1, float c2, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    adam_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, p, g, m, v, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+}  // namespace hrir

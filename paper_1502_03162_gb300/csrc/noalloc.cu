@@ -123,6 +123,7 @@ extern "C" int hrir_render_batch_noalloc(hrir_ctx *ctx, int n_src, int64_t len, 
     a.table = sparse ? ctx->d_sparse : reinterpret_cast<const unsigned char *>(ctx->d_dense);
     a.rec_bytes = rec_bytes;
     a.nchunk = sparse ? ctx->sparse_nch_pad : nchunk;
+    a.nseg = sparse ? ctx->sparse_nchunk : 0;
     a.halo = halo;
     a.buf_elems = buf_elems;
     a.full_rows = (int)(len / kMixBox);

@@ -14,12 +14,13 @@ namespace {
 constexpr int kBlk = 2048;
 constexpr int kThreads = 256;
 constexpr int kMaxRes = 512;
+constexpr int kMaxSpanTiles = 16;   // partial tiles one block's z span may touch
 
 __global__ void __launch_bounds__(kThreads) reduce_fir_kernel(const ReduceArgs a)
 {
     __shared__ float zs[kBlk + kMaxRes - 1];
     __shared__ float fs[kMaxRes];
-    __shared__ int nslots[2];
+    __shared__ int nslots[kMaxSpanTiles];
     const int e = blockIdx.y;
     const int64_t n0 = (int64_t)blockIdx.x * kBlk;
     const int lf = a.res ? a.res_len : 1;
@@ -27,10 +28,8 @@ __global__ void __launch_bounds__(kThreads) reduce_fir_kernel(const ReduceArgs a
     const int64_t m_hi = n0 + kBlk;  // exclusive
     const int64_t z_len = (int64_t)a.n_tiles * a.tile;
     const int t_lo = (int)((m_lo > 0 ? m_lo : 0) / a.tile);
-    if (threadIdx.x == 0) {
-        nslots[0] = t_lo < a.n_tiles ? a.part.slots(t_lo) : 0;
-        nslots[1] = t_lo + 1 < a.n_tiles ? a.part.slots(t_lo + 1) : 0;
-    }
+    for (int k = threadIdx.x; k < kMaxSpanTiles; k += kThreads)
+        nslots[k] = t_lo + k < a.n_tiles ? a.part.slots(t_lo + k) : 0;
     for (int l = threadIdx.x; l < lf; l += kThreads) fs[l] = a.res ? a.res[e * a.res_len + l] : 1.0f;
     __syncthreads();
     const int span = (int)(m_hi - m_lo);
@@ -66,7 +65,9 @@ __global__ void __launch_bounds__(kThreads) reduce_fir_kernel(const ReduceArgs a
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st)
 {
     if (a.out_len <= 0) return cudaSuccess;
-    if ((a.res ? a.res_len : 1) > kMaxRes || a.tile < kBlk + kMaxRes) return cudaErrorInvalidValue;
+    if ((a.res ? a.res_len : 1) > kMaxRes || a.tile < 1 ||
+        (kBlk + kMaxRes - 2) / a.tile + 2 > kMaxSpanTiles)
+        return cudaErrorInvalidValue;
     dim3 grid((unsigned)((a.out_len + kBlk - 1) / kBlk), 2);
     reduce_fir_kernel<<<grid, kThreads, 0, st>>>(a);
     return cudaGetLastError();

@@ -87,7 +87,9 @@ __global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, 
 // segment of seg_len filter offsets at a time:
 //   int4  {n_seg, 0, 0, 0}
 //   int2  cnt[nseg_pad] {left taps, right taps} of each segment
-//   int2  tap[...] {TMEM column, weight bits}: per segment, its left then its right taps
+//   int2  tap[...] {TMEM column, weight bits}: per segment, its left then its right taps,
+//         each list padded to an even length with a zero-weight tap at column 1, then 4
+//         zero-weight entries (the kernel reads two taps ahead)
 // A tap at offset o of segment s reads window columns (s+1) seg_len - o onward.
 __global__ void build_sparse_records_kernel(const uint16_t *__restrict__ idx,
                                             const float *__restrict__ w,
@@ -119,9 +121,14 @@ __global__ void build_sparse_records_kernel(const uint16_t *__restrict__ idx,
                 taps[o++] = make_int2(hi - i, __float_as_int(w[row + t]));
                 ++n_e[e];
             }
+            if (n_e[e] & 1) {
+                taps[o++] = make_int2(1, 0);
+                ++n_e[e];
+            }
         }
         cnt[s] = make_int2(n_e[0], n_e[1]);
     }
+    for (int p = 0; p < 4; ++p) taps[o++] = make_int2(1, 0);
     *hdr = make_int4(n_seg, 0, 0, 0);
 }
 

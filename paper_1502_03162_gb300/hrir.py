@@ -49,11 +49,21 @@ SIGNATURES = {
     "hrir_stream_stats": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_int64)], _i),
     "hrir_stream_close": ([_vp], _i),
+    "hrir_mlp_param_count": ([_i], _i64),
+    "hrir_mlp_act_stride": ([_i], _i64),
+    "hrir_mlp_forward": ([_vp, _i64, _vp, _i, _vp, _vp, _vp, _vp], _i),
+    "hrir_mlp_backward": ([_vp, _i64, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i),
+    "hrir_mlp_adam": ([_vp, _i64, _vp, _vp, _vp, _vp, _i, ctypes.c_float, ctypes.c_float,
+                       ctypes.c_float, ctypes.c_float, _vp], _i),
+    "hrir_render_moving": ([_vp, _i, _i64, _i64, _vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _i64,
+                            _vp], _i),
+    "hrir_resonance_per_source": ([_vp, _i, _i64, _i64, _i, _vp, _i, _vp, _i64, _vp], _i),
     "hrir_set_timing": ([_vp, _i], _i),
     "hrir_kernel_times": ([_vp, _vp, _vp, _i], _i),
 }
 HRIR_K_COUNT = 8
-KERNEL_NAMES = {0: "mix_sparse", 1: "mix_dense", 2: "reduce_fir", 3: "fft", 4: "tables"}
+KERNEL_NAMES = {0: "mix_sparse", 1: "mix_dense", 2: "reduce_fir", 3: "fft", 4: "tables",
+                5: "mlp", 6: "mix_moving", 7: "resonance_gemm"}
 
 _lib = None
 _lock = threading.Lock()
@@ -162,6 +172,7 @@ def hrir_load_filters(ctx, tap_idx, tap_w, tap_nnz, refl_len: int, res, fft_size
         ctx, n_dirs, n_ears, refl_len, k_max, tap_idx.ctypes.data, tap_w.ctypes.data,
         tap_nnz.ctypes.data, res.shape[1], res.ctypes.data, fft_size)
     _check(ctx, rc)
+    _RES_LEN[ctx] = res.shape[1]
 
 
 def hrir_out_len(ctx, length: int, full: bool = True) -> int:
@@ -312,6 +323,121 @@ class Stream:
 
     def close(self):
         hrir_stream_close(self.r.ctx)
+
+
+def hrir_mlp_param_count(refl_len: int) -> int:
+    return load_library().hrir_mlp_param_count(refl_len)
+
+
+def hrir_mlp_act_stride(refl_len: int) -> int:
+    return load_library().hrir_mlp_act_stride(refl_len)
+
+
+def _f32_cuda(t, shape=None):
+    import torch
+    assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    if shape is not None:
+        assert tuple(t.shape) == tuple(shape), (tuple(t.shape), shape)
+    return t.data_ptr()
+
+
+def hrir_mlp_forward(ctx, dirs, params, refl_len: int, out=None, acts=None, stream=None):
+    """dirs: CUDA float32 [n][3] (az, el, ear = -1/+1); params: CUDA float32 [param_count].
+    Returns out [n][refl_len] (and fills acts [n][act_stride] when given)."""
+    import torch
+    n = dirs.shape[0]
+    if out is None:
+        out = torch.empty((n, refl_len), dtype=torch.float32, device=dirs.device)
+    rc = load_library().hrir_mlp_forward(
+        ctx, n, _f32_cuda(dirs, (n, 3)), refl_len,
+        _f32_cuda(params, (hrir_mlp_param_count(refl_len),)), _f32_cuda(out, (n, refl_len)),
+        _f32_cuda(acts, (n, hrir_mlp_act_stride(refl_len))) if acts is not None else None,
+        _stream_handle(stream))
+    _check(ctx, rc)
+    return out
+
+
+def hrir_mlp_backward(ctx, dirs, params, acts, out, target, refl_len: int, grads=None,
+                      loss=None, stream=None):
+    """Gradient of L = 1/(2n) sum ||out - target||^2; returns (grads, loss) CUDA tensors."""
+    import torch
+    n = dirs.shape[0]
+    P = hrir_mlp_param_count(refl_len)
+    if grads is None:
+        grads = torch.empty(P, dtype=torch.float32, device=dirs.device)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=dirs.device)
+    rc = load_library().hrir_mlp_backward(
+        ctx, n, _f32_cuda(dirs, (n, 3)), refl_len, _f32_cuda(params, (P,)),
+        _f32_cuda(acts, (n, hrir_mlp_act_stride(refl_len))), _f32_cuda(out, (n, refl_len)),
+        _f32_cuda(target, (n, refl_len)), _f32_cuda(grads, (P,)), _f32_cuda(loss),
+        _stream_handle(stream))
+    _check(ctx, rc)
+    return grads, loss
+
+
+def hrir_mlp_adam(ctx, params, grads, m, v, step: int, lr: float, beta1=0.9, beta2=0.999,
+                  eps=1e-8, stream=None) -> None:
+    n = params.numel()
+    rc = load_library().hrir_mlp_adam(ctx, n, _f32_cuda(params), _f32_cuda(grads, (n,)),
+                                      _f32_cuda(m, (n,)), _f32_cuda(v, (n,)), int(step),
+                                      float(lr), float(beta1), float(beta2), float(eps),
+                                      _stream_handle(stream))
+    _check(ctx, rc)
+
+
+def hrir_render_moving(ctx, src, tap_idx, tap_w, tap_nnz, seg_len: int, full=True, length=None,
+                       out=None, stream=None):
+    """src: CUDA float32 [S][ld]; tap tables CUDA [S][n_seg][2][k] (idx int16 holding uint16,
+    w float32) and nnz uint8 [S][n_seg][2].  Returns out CUDA float32 [2][out_len]."""
+    import torch
+    assert src.is_cuda and src.dtype == torch.float32 and src.dim() == 2 and src.stride(1) == 1
+    S = src.shape[0]
+    ld = src.stride(0) if S > 1 else src.shape[1]
+    L = src.shape[1] if length is None else int(length)
+    n_seg, k = tap_idx.shape[1], tap_idx.shape[3]
+    assert tuple(tap_idx.shape) == (S, n_seg, 2, k) and tap_idx.is_contiguous()
+    assert tuple(tap_w.shape) == (S, n_seg, 2, k) and tap_w.is_contiguous()
+    assert tuple(tap_nnz.shape) == (S, n_seg, 2) and tap_nnz.is_contiguous()
+    out_len = hrir_out_len(ctx, L, full)
+    if out is None:
+        out = torch.empty((2, max(out_len, 1)), dtype=torch.float32, device=src.device)
+    rc = load_library().hrir_render_moving(
+        ctx, S, L, ld, src.data_ptr(), n_seg, int(seg_len), k, tap_idx.data_ptr(),
+        tap_w.data_ptr(), tap_nnz.data_ptr(), int(full), out.data_ptr(), out.stride(0),
+        _stream_handle(stream))
+    _check(ctx, rc)
+    return out[:, :out_len]
+
+
+def hrir_resonance_per_source(ctx, src, full=True, length=None, out=None, stream=None):
+    """src: CUDA bfloat16/float16 [S][ld].  Returns u: CUDA float32 [S][2][out_len] with
+    u[s, e] = y_s * f_e (the loaded resonance), computed on the tensor cores."""
+    import torch
+    assert src.is_cuda and src.dim() == 2 and src.stride(1) == 1
+    assert src.dtype in (torch.bfloat16, torch.float16)
+    S = src.shape[0]
+    ld = src.stride(0) if S > 1 else src.shape[1]
+    L = src.shape[1] if length is None else int(length)
+    res_len = _res_len(ctx)
+    out_len = (L + res_len - 1 if L > 0 else 0) if full else L
+    if out is None:
+        out = torch.empty((S, 2, max((out_len + 3) // 4 * 4, 4)), dtype=torch.float32,
+                          device=src.device)
+    assert out.is_cuda and out.dtype == torch.float32 and out.stride(2) == 1
+    assert out.stride(0) == 2 * out.stride(1)
+    rc = load_library().hrir_resonance_per_source(ctx, S, L, ld, _dtype_code(src), src.data_ptr(),
+                                                  int(full), out.data_ptr(), out.stride(1),
+                                                  _stream_handle(stream))
+    _check(ctx, rc)
+    return out[:, :, :out_len]
+
+
+_RES_LEN = {}
+
+
+def _res_len(ctx) -> int:
+    return _RES_LEN[ctx]
 
 
 def hrir_set_timing(ctx, enable: bool) -> None:

@@ -126,3 +126,91 @@ def batched_config(S: int = 1024, L: int = 480000, seed: int = 2, ld: int | None
     dirs = directions(rng, S, n_dirs)
     y = sources_ar1(rng, S, L, ld, out=out)
     return dict(y=y, dirs=dirs, G=G, res=res)
+
+
+# ---------------------------------------------------------------------------------------
+# synthetic HRIR sets for the learned filters (stand-ins for measured HRIR databases)
+# ---------------------------------------------------------------------------------------
+def hrir_set_params(seed: int, n_refl: int = 10, refl_len: int = REFL_LEN,
+                    res_len: int = RES_LEN) -> dict:
+    """Parameters of one seeded synthetic HRIR set.
+
+    Per ear: a 32-tap resonance (as `resonance`).  Reflections k = 0..n_refl-1, k = 0 being
+    the direct path at delay 0: base delay d0_k, delay swing a_k with phase p_k, gain
+    c0_k with a gain swing of up to 40% and phase q_k.  The right ear mirrors the azimuth."""
+    rng = rng_for(seed)
+    res = resonance(rng, res_len)
+    d0 = np.concatenate([[0.0], np.sort(rng.uniform(8.0, refl_len - 40.0, n_refl - 1))])
+    amp = np.concatenate([[0.0], rng.uniform(0.5, 4.0, n_refl - 1)])
+    return dict(res=res, d0=d0, amp=amp, phase=rng.uniform(0, 2 * np.pi, n_refl),
+                gain=np.concatenate([[1.0], rng.uniform(0.15, 0.6, n_refl - 1)]),
+                gswing=rng.uniform(0.0, 0.4, n_refl), gphase=rng.uniform(0, 2 * np.pi, n_refl),
+                refl_len=refl_len)
+
+
+def hrir_set_reflections(p: dict, az, el, ear) -> np.ndarray:
+    """Non-negative reflection rows [n][refl_len] at arbitrary directions (radians; ear 0
+    left, 1 right): each reflection is a two-tap linear-interpolation pulse at its delay
+    d0 + a cos(az' - p) cos(el), az' = az (left) or -az (right)."""
+    az = np.asarray(az, dtype=np.float64)
+    el = np.asarray(el, dtype=np.float64)
+    ear = np.asarray(ear)
+    azs = np.where(ear == 0, az, -az)
+    n = az.size
+    Lg = p["refl_len"]
+    g = np.zeros((n, Lg))
+    rows = np.arange(n)
+    for k in range(p["d0"].size):
+        d = p["d0"][k] + p["amp"][k] * np.cos(azs - p["phase"][k]) * np.cos(el)
+        d = np.clip(d, 0.0, Lg - 1.001)
+        c = p["gain"][k] * (1.0 + p["gswing"][k] * np.cos(azs - p["gphase"][k]) * np.cos(el)) \
+            * np.exp(-d / 60.0)
+        i0 = np.floor(d).astype(np.int64)
+        fr = d - i0
+        np.add.at(g, (rows, i0), c * (1.0 - fr))
+        np.add.at(g, (rows, i0 + 1), c * fr)
+    return g
+
+
+def hrir_set_at(p: dict, az, el, ear) -> np.ndarray:
+    """HRIRs [n][H] (H = Lf + Lg - 1) at arbitrary directions: the resonance of the ear
+    followed by its reflections, scaled to absolute sum 1 (the paper's HRIR preprocessing
+    normalises every HRIR that way).  Data generation only: this stands in for measured
+    HRIRs, it is not part of the rendering path."""
+    g = hrir_set_reflections(p, az, el, ear)
+    ear = np.asarray(ear)
+    res = p["res"].astype(np.float64)
+    H = res.shape[1] + g.shape[1] - 1
+    x = np.zeros((g.shape[0], H))
+    for i in range(g.shape[0]):
+        x[i] = np.convolve(res[int(ear[i])], g[i])
+    return x / np.sum(np.abs(x), axis=1, keepdims=True)
+
+
+def hrir_set(seed: int, **kw):
+    """One synthetic HRIR set on the 25 x 50 grid: (X [1250][2][H], az [1250], el [1250],
+    params)."""
+    p = hrir_set_params(seed, **kw)
+    az, el = az_el_grid()
+    n = az.size
+    X = np.stack([hrir_set_at(p, az, el, np.full(n, e)) for e in range(2)], axis=1)
+    return X, az, el, p
+
+
+def trajectories(rng: np.random.Generator, S: int, n_seg: int):
+    """Moving-source directions per (source, segment): smooth random walks over the grid's
+    azimuth/elevation range.  Returns (az, el) radians [S][n_seg]."""
+    az_lo, az_hi = np.deg2rad(-80.0), np.deg2rad(80.0)
+    el_lo, el_hi = np.deg2rad(-45.0), np.deg2rad(230.0)
+    az0 = rng.uniform(az_lo, az_hi, S)
+    el0 = rng.uniform(el_lo, el_hi, S)
+    vaz = rng.uniform(-1.0, 1.0, S) * np.deg2rad(0.5)     # per segment (~90 deg/s at 48 kHz)
+    vel = rng.uniform(-1.0, 1.0, S) * np.deg2rad(0.5)
+    t = np.arange(n_seg)[None, :]
+    az = az0[:, None] + vaz[:, None] * t
+    el = el0[:, None] + vel[:, None] * t
+    # reflect at the range edges
+    span_a, span_e = az_hi - az_lo, el_hi - el_lo
+    az = az_lo + span_a - np.abs(np.mod(az - az_lo, 2 * span_a) - span_a)
+    el = el_lo + span_e - np.abs(np.mod(el - el_lo, 2 * span_e) - span_e)
+    return az, el
