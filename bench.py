@@ -271,10 +271,12 @@ def bench_learned(rend, torch, seed=13, S=4096, L=96000, seg=256, k=16, train_st
     w = torch.empty((S, n_seg, 2, k), dtype=torch.float32, device="cuda")
     nnz = torch.empty((S, n_seg, 2), dtype=torch.uint8, device="cuda")
     out = torch.empty((2, L + 230), dtype=torch.float32, device="cuda")
-    infer = lambda: hrir.hrir_mlp_forward(rend.ctx, rows, params, 200, out=g)  # noqa: E731
+    infer32 = lambda: hrir.hrir_mlp_forward(rend.ctx, rows, params, 200, out=g)  # noqa: E731
+    infer = lambda: hrir.hrir_mlp_forward_bf16(rend.ctx, rows, params, 200, out=g)  # noqa: E731
     pack = lambda: hrir.hrir_topk_pack(rend.ctx, g.view(S, n_seg, 2, 200), k, idx, w, nnz)  # noqa: E731
     render = lambda: hrir.hrir_render_moving(rend.ctx, y, idx, w, nnz, seg, out=out)  # noqa: E731
     nb = lambda: None  # noqa: E731
+    t_inf32 = time_steps(infer32, 2, 1, torch, nb)
     t_inf = time_steps(infer, 3, 1, torch, nb)
     t_pack = time_steps(pack, 3, 1, torch, nb)
     t_ren = time_steps(render, 5, 2, torch, nb)
@@ -308,8 +310,11 @@ def bench_learned(rend, torch, seed=13, S=4096, L=96000, seg=256, k=16, train_st
                         f"network filters top-{k}, linear crossfade",
             "render": {"value": units / (t_ren / 1e3), "unit": "source-ear samples/s",
                        "ms": t_ren, "fp32_tflops": 4.0 * k * units / (t_ren / 1e3) / 1e12},
-            "filters": {"rows": n_rows, "ms": t_inf, "rows_per_s": n_rows / (t_inf / 1e3),
-                        "fp32_tflops": flops_fwd_row * n_rows / (t_inf / 1e3) / 1e12,
+            "filters": {"rows": n_rows, "precision": "bf16 tensor cores", "ms": t_inf,
+                        "rows_per_s": n_rows / (t_inf / 1e3),
+                        "tflops": flops_fwd_row * n_rows / (t_inf / 1e3) / 1e12,
+                        "fp32_simt_ms": t_inf32,
+                        "fp32_simt_tflops": flops_fwd_row * n_rows / (t_inf32 / 1e3) / 1e12,
                         "topk_ms": t_pack},
             "end_to_end": {"value": units / ((t_inf + t_pack + t_ren) / 1e3),
                            "unit": "source-ear samples/s", "ms": t_inf + t_pack + t_ren},

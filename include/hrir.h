@@ -232,6 +232,10 @@ int hrir_render_batch_noalloc(hrir_ctx *ctx, int n_src, int64_t len, int64_t src
  * hrir_mlp_act_stride   row stride of acts (floats).
  * hrir_mlp_forward      out [n_rows][Lg] = g for every row; acts is filled when not NULL
  *                       (otherwise the context workspace holds the activations in chunks).
+ * hrir_mlp_forward_bf16 the same filters for inference on the tensor cores: weights and
+ *                       activations rounded to BF16, FP32 accumulation, FP32 output
+ *                       (Lg <= 256; no activations kept).  For the millions of rows of moving
+ *                       sources; agrees with hrir_mlp_forward to BF16 precision.
  * hrir_mlp_backward     grads [param_count] = dL/dparams for the batch whose forward pass left
  *                       `acts` and `out`; target [n_rows][Lg]; loss (device float, may be
  *                       NULL) = L.  1 <= n_rows <= 2^24.  Deterministic (fixed-order sums).
@@ -243,6 +247,8 @@ int64_t hrir_mlp_param_count(int refl_len);
 int64_t hrir_mlp_act_stride(int refl_len);
 int hrir_mlp_forward(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl_len,
                      const float *params, float *out, float *acts, void *stream);
+int hrir_mlp_forward_bf16(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl_len,
+                          const float *params, float *out, void *stream);
 int hrir_mlp_backward(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl_len,
                       const float *params, const float *acts, const float *out,
                       const float *target, float *grads, float *loss, void *stream);

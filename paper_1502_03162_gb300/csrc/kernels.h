@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 
 #include "common.cuh"
 
@@ -28,7 +29,11 @@ constexpr int kSparseTile = kSparseQuarters * 32 * kSparseR;
 constexpr int kSparseTmemCols = 256;
 constexpr int kSparseSegment = kSparseTmemCols - kSparseR;  // 204
 constexpr int kDenseR = HRIR_DENSE_R, kDenseWarps = HRIR_DENSE_WARPS;
-constexpr int kMixMaxStages = 4;
+constexpr int kMixMaxStages = 6;
+constexpr int kMixDirCache = 2048;                // unit directions staged in shared memory
+// shared memory after the stage ring and its barriers: abort flag + TMEM slot (16 B), the
+// per-stage release counters and last issued units, the direction cache
+constexpr int kMixSmemTail = 16 + 2 * kMixMaxStages * 4 + kMixDirCache * 4;
 constexpr int kMixBox = 256;                      // TMA box width (elements)
 constexpr int kRunSources = 64;                   // max sources per register accumulation run
 
@@ -160,6 +165,25 @@ cudaError_t launch_colsum(int64_t rows, int N, const float *D, int64_t ldd, floa
 cudaError_t launch_split_reduce(int splits, int M, int N, const float *P, float *out, cudaStream_t st);
 cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v, float lr, float b1,
                         float b2, float eps, float c1, float c2, cudaStream_t st);
+
+// One layer of the network's BF16 tensor-core inference: Z = H W^T + b (K = 256) over 128-row
+// tiles; first: H = relu(W1 x + b1) from the rows' features; last: out = softplus(Z) (FP32),
+// else hout = relu(Z) (BF16).
+struct MlpTcArgs {
+    int64_t n_rows;
+    const float *dirs;           // [n_rows][3] (first layer only)
+    const float *W1, *b1;        // first layer only
+    int first, last;
+    const __nv_bfloat16 *in;     // [n_rows][256] (not first)
+    const float *W;              // [N][256] FP32 (converted to BF16 in shared memory)
+    const float *b;              // [N]
+    int N, n_pad;                // N <= n_pad <= 256, n_pad % 16 == 0
+    __nv_bfloat16 *hout;         // [n_rows][256] (not last)
+    float *out;                  // [n_rows][N] (last)
+    int *status;
+};
+size_t mlp_tc_smem_bytes(int n_pad);
+cudaError_t launch_mlp_layer_tc(const MlpTcArgs &a, int grid, cudaStream_t st);
 
 // ---- moving sources: per-segment filters with a linear crossfade ---------------------------
 constexpr int kMovTile = 1024;   // outputs per (tile, source) unit

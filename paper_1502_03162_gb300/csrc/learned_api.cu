@@ -35,6 +35,8 @@ int64_t act_stride(int refl_len) { return round_up(3 * H + refl_len, 4); }
 
 // Rows per forward chunk when the caller keeps no activations.
 constexpr int64_t kFwdChunk = 1 << 16;
+// Rows per chunk of the tensor-core inference (two BF16 activation buffers of 256 columns).
+constexpr int64_t kTcChunk = 1 << 19;
 
 int grow_ws(hrir_ctx *ctx, size_t need)
 {
@@ -130,6 +132,51 @@ int hrir_mlp_forward(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl_
         g.H = out + r0 * refl_len;
         g.ldh = refl_len;
         HRIR_CUDA_TRY(ctx, launch_gemm(1, true, false, g, 1, st));
+    }
+    kt.done();
+    return HRIR_OK;
+}
+
+int hrir_mlp_forward_bf16(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl_len,
+                          const float *params, float *out, void *stream)
+{
+    if (!ctx) return fail(nullptr, HRIR_EINVAL, "ctx is NULL");
+    if (n_rows < 0 || refl_len < 1 || refl_len > 256)
+        return fail(ctx, HRIR_EINVAL, "bad sizes (n_rows=%lld refl_len=%d; refl_len <= 256)",
+                    (long long)n_rows, refl_len);
+    if (n_rows == 0) return HRIR_OK;
+    if (!dirs || !params || !out) return fail(ctx, HRIR_EINVAL, "NULL buffer");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HRIR_ECUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    const MlpLayout L(refl_len);
+    const int64_t chunk = std::min<int64_t>(n_rows, kTcChunk);
+    int rc = grow_ws(ctx, (size_t)chunk * H * 2 * sizeof(__nv_bfloat16));
+    if (rc) return rc;
+    __nv_bfloat16 *h1 = static_cast<__nv_bfloat16 *>(ctx->d_mlp_ws);
+    __nv_bfloat16 *h2 = h1 + (size_t)chunk * H;
+    KernelTimer kt(ctx, HRIR_K_MLP, st);
+    for (int64_t r0 = 0; r0 < n_rows; r0 += chunk) {
+        const int64_t nb = std::min(chunk, n_rows - r0);
+        const int grid = (int)std::min<int64_t>(ctx->num_sms, (nb + 127) / 128);
+        MlpTcArgs a{};
+        a.n_rows = nb;
+        a.dirs = dirs + r0 * 3;
+        a.W1 = params + L.W1;
+        a.b1 = params + L.b1;
+        a.status = ctx->d_status;
+        // layer 2 (layer 1 fused), layer 3, output layer
+        for (int l = 0; l < 3; ++l) {
+            a.first = l == 0;
+            a.last = l == 2;
+            a.in = l == 1 ? h1 : h2;
+            a.W = params + (l == 0 ? L.W2 : l == 1 ? L.W3 : L.W4);
+            a.b = params + (l == 0 ? L.b2 : l == 1 ? L.b3 : L.b4);
+            a.N = l == 2 ? refl_len : H;
+            a.n_pad = (int)round_up(a.N, 16);
+            a.hout = l == 0 ? h1 : h2;
+            a.out = out + r0 * refl_len;
+            HRIR_CUDA_TRY(ctx, launch_mlp_layer_tc(a, grid, st));
+        }
     }
     kt.done();
     return HRIR_OK;

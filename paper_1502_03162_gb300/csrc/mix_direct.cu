@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
 
 size_t mix_smem_bytes(int buf_elems, int elem_bytes, int rec_bytes, int stages)
 {
-    return (size_t)stages * ((size_t)buf_elems * elem_bytes + rec_bytes) + 2 * stages * 8 + 16;
+    return (size_t)stages * ((size_t)buf_elems * elem_bytes + rec_bytes) + 2 * stages * 8 + kMixSmemTail;
 }
 
 MixShape mix_shape(int mode)

@@ -19,10 +19,9 @@
 // -> tcgen05.st) into the other, the left-ear warp before its taps and the right-ear warp
 // after them; a named barrier per pair (with
 // an AND vote, so that both warps leave together on a timeout) hands the buffers over.
-// Warp 0 also keeps a shared-memory ring filled with each unit's source tile (tensor TMA,
-// 256-sample halo, hardware zero fill outside [0, len)) and the direction's tap record
-// (bulk copy), issuing into stages as they free up without blocking unless the next window
-// needs the unit.  Work is a persistent balanced range of units per CTA; register accumulators are
+// A ring of up to 6 shared-memory stages holds each unit's source tile (tensor TMA, 256-sample
+// halo, hardware zero fill outside [0, len)) and the direction's tap record (bulk copy): the
+// last of the 8 warps to release a stage refills it at once with the unit `stages` ahead.  Work is a persistent balanced range of units per CTA; register accumulators are
 // flushed every <= 64 sources into partial slots that the reduction sums in a fixed order.
 // All waits are bounded.
 #include <cuda_bf16.h>
@@ -305,6 +304,9 @@ __global__ void __launch_bounds__(NW * 32, 1)
     uint64_t *bars = reinterpret_cast<uint64_t *>(rbuf + (size_t)stages * a.rec_bytes);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * stages);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages) + 1;
+    int *relcnt = reinterpret_cast<int *>(bars + 2 * stages) + 4;      // [kMixMaxStages]
+    int *last_issued = relcnt + kMixMaxStages;                         // [kMixMaxStages]
+    int *dircache = last_issued + kMixMaxStages;                       // [kMixDirCache]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -315,6 +317,10 @@ __global__ void __launch_bounds__(NW * 32, 1)
             mbar_init(smem_addr(&bars[stages + i]), NW);    // empty: one arrive per warp
         }
         *abort_flag = 0;
+        for (int i = 0; i < kMixMaxStages; ++i) {
+            relcnt[i] = 0;
+            last_issued[i] = -1;
+        }
         mbar_fence_init();
     }
     if (warp == 0) {
@@ -331,29 +337,40 @@ __global__ void __launch_bounds__(NW * 32, 1)
     const int64_t u_begin = a.part.first(blockIdx.x);
     const int64_t u_end = a.part.first(blockIdx.x + 1);
     const int64_t n_units = u_end - u_begin;
-    int64_t issued = 0;  // units issued (warp 0)
-    int next_dir = n_units > 0 ? raw_dir(a, u_begin) : 0;  // direction of unit `issued`, in flight
+    // directions of this CTA's first kMixDirCache units, staged once
+    const int n_cached = (int)(n_units < kMixDirCache ? n_units : kMixDirCache);
+    for (int i = threadIdx.x; i < n_cached; i += blockDim.x) dircache[i] = raw_dir(a, u_begin + i);
+    __syncthreads();
 
-    // Warp 0: issue units into free stages; those up to `must` are waited for (bounded), the
-    // rest only if their stage is already free.  Returns false on a timeout.
-    auto fill = [&](int64_t must) {
-        while (issued < n_units) {
-            const int st = (int)(issued % stages);
-            if (issued >= stages) {
-                const uint32_t eb = smem_addr(&bars[stages + st]);
-                const uint32_t par = (uint32_t)((issued / stages - 1) & 1);
-                if (issued <= must) {
-                    if (!mbar_wait_bounded(eb, par, abort_flag, a.status)) return false;
-                } else if (!mbar_test_wait(eb, par)) {
-                    break;
-                }
-            }
-            const int d = checked_dir(a, next_dir, lane);
-            issue_unit<T>(&tmap, &tmap3, a, u_begin + issued, d, ybuf + (size_t)st * a.buf_elems,
-                          rbuf + (size_t)st * a.rec_bytes, smem_addr(&bars[st]), lane);
-            ++issued;
-            if (issued < n_units) next_dir = raw_dir(a, u_begin + issued);
+    // Issue unit k (local index) into its stage (all lanes of the calling warp).
+    auto issue = [&](int64_t k) {
+        const int st = (int)(k % stages);
+        const int d = checked_dir(a, k < n_cached ? dircache[k] : raw_dir(a, u_begin + k), lane);
+        issue_unit<T>(&tmap, &tmap3, a, u_begin + k, d, ybuf + (size_t)st * a.buf_elems,
+                      rbuf + (size_t)st * a.rec_bytes, smem_addr(&bars[st]), lane);
+        if (lane == 0) last_issued[st] = (int)k;
+    };
+    // A warp is done with unit k's stage: arrive on its empty barrier; the last of the NW
+    // warps to arrive refills the stage with unit k + stages at once.  Returns false on a
+    // timeout.
+    auto release = [&](int64_t k) {
+        const int st = (int)(k % stages);
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            mbar_arrive(smem_addr(&bars[stages + st]));
+            last = atomicAdd(&relcnt[st], 1) == NW - 1;
         }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (!last) return true;
+        if (lane == 0) relcnt[st] = 0;
+        if (k + stages >= n_units) return true;
+        // every warp has arrived: the phase completes (its acquire orders their reads of the
+        // stage before the copy that overwrites it)
+        if (!mbar_wait_bounded(smem_addr(&bars[stages + st]), (uint32_t)((k / stages) & 1),
+                               abort_flag, a.status))
+            return false;
+        issue(k + stages);
         return true;
     };
 
@@ -375,8 +392,9 @@ __global__ void __launch_bounds__(NW * 32, 1)
                    kHalf * ear;
         };
         // prologue: fill the ring, the first window into buffer 0
-        bool ok = warp == 0 ? fill(0) : true;
-        ok = ok && mbar_wait_bounded(smem_addr(&bars[0]), 0u, abort_flag, a.status);
+        if (warp == 0)
+            for (int64_t k0 = 0; k0 < n_units && k0 < stages; ++k0) issue(k0);
+        bool ok = mbar_wait_bounded(smem_addr(&bars[0]), 0u, abort_flag, a.status);
         if (ok) copy_half<T>(window_src(0, 0), tq + (uint32_t)(kHalf * ear));
         tm_wait_st();
         ok = pair_sync_all(q, ok);
@@ -391,8 +409,8 @@ __global__ void __launch_bounds__(NW * 32, 1)
                 k1 = k + 1;
             }
             const bool have_next = k1 < n_units;
-            bool ok_next = warp == 0 ? fill(k1) : true;
-            if (ok_next && have_next && s1 == 0)
+            bool ok_next = true;
+            if (have_next && s1 == 0)
                 ok_next = mbar_wait_bounded(smem_addr(&bars[k1 % stages]),
                                             (uint32_t)((k1 / stages) & 1), abort_flag, a.status);
             // the next window's half: the left-ear warp copies it before its taps, the
@@ -409,6 +427,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
                                (ear ? c.x : 0);
             apply_taps(acc, tq + (uint32_t)(kCols * (j & 1)), taps, ear ? c.y : c.x);
             toff += c.x + c.y;
+            if (s == n_seg - 1 && !release(k)) ok_next = false;   // last read of unit k's stage
             if (copy && ear == 1) copy_half<T>(nsrc, ndst);
             tm_wait_st();
             ok = pair_sync_all(q, ok_next);
@@ -421,8 +440,6 @@ __global__ void __launch_bounds__(NW * 32, 1)
                     slot = a.part.slot_base(blockIdx.x, t);
                     run_n = 0;
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_addr(&bars[stages + (int)(k % stages)]));
                 ++run_n;
                 const bool tile_end = (u + 1 == u_end) || ((u + 1) / a.n_src != t);
                 if (run_n == a.part.gs || tile_end) {
@@ -447,9 +464,11 @@ __global__ void __launch_bounds__(NW * 32, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0) {
         // let every copy still in flight land before the CTA exits (bounded; immediate unless
-        // a wait timed out)
-        for (int64_t j = issued > stages ? issued - stages : 0; j < issued; ++j) {
-            const uint32_t fb = smem_addr(&bars[j % stages]);
+        // a wait timed out): the last unit issued into each stage
+        for (int st = 0; st < stages; ++st) {
+            const int j = last_issued[st];
+            if (j < 0) continue;
+            const uint32_t fb = smem_addr(&bars[st]);
             const uint32_t par = (uint32_t)((j / stages) & 1);
             const uint64_t t0 = global_timer_ns();
             while (!mbar_try_wait(fb, par) && global_timer_ns() - t0 < kWaitLimitNs) {

@@ -1,0 +1,226 @@
+// mlp_tc.cu -- bulk inference of the direction -> reflection-filter network on the tensor
+// cores (BF16 operands, FP32 accumulation in tensor memory), for the millions of
+// (source, segment, ear) rows of moving sources.
+//
+// One kernel per layer l = 2, 3, 4:  Z[r][n] = sum_k H[r][k] W_l[n][k] + b_l[n] (K = 256),
+// H = relu(z_{l-1}).  Each CTA (persistent over 128-row tiles) keeps W_l in shared memory in
+// the canonical no-swizzle K-major layout (8-row x 16-byte core matrices) and, per tile,
+// builds the A operand (for layer 2 straight from the features: z1 = W1 x + b1, ReLU, so
+// layer 1 is fused on the CUDA cores), issues 16 tcgen05.mma (K = 16 each, M = 128,
+// N = 256 or Lg rounded up to 16) from one thread, commits to an mbarrier, and the 4 warps
+// read their 32 accumulator rows with tcgen05.ld and apply bias + ReLU (hidden layers,
+// stored as BF16 for the next layer) or bias + softplus (output layer, stored as FP32).
+// Waits are bounded.
+#include <cuda_bf16.h>
+
+#include "kernels.h"
+
+namespace hrir {
+
+namespace {
+
+constexpr int kRows = 128;                  // MMA M: rows per tile
+constexpr int kK = kMlpHidden;              // 256
+constexpr int kKc = kK / 8;                 // core matrices along K
+constexpr int kThreads = 128;
+constexpr uint32_t kTmemCols = 256;
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// kind::f16, D FP32, A and B BF16, both K-major
+__host__ __device__ constexpr uint32_t instr_desc_bf16(uint32_t M, uint32_t N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ int core_off(int row, int k) { return (row >> 3) * (kKc * 64) + (k >> 3) * 64 + (row & 7) * 8 + (k & 7); }
+
+// two floats -> BF16 pair (round to nearest), the first in the low half
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&p);
+}
+
+__device__ __forceinline__ float softplus_f(float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); }
+
+__device__ __forceinline__ void tm_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __nv_bfloat16 *Wm = reinterpret_cast<__nv_bfloat16 *>(smem);        // [n_pad][256] canonical
+    __nv_bfloat16 *Am = Wm + (size_t)a.n_pad * kK;                       // [128][256] canonical
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Am + kRows * kK);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    int *abort_flag = reinterpret_cast<int *>(bar + 1) + 1;
+    float *w1 = reinterpret_cast<float *>(bar + 2);                      // layer 2: W1 [256][5], b1 [256]
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(smem_addr(bar), 1);
+        *abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // this layer's weights (rows n >= N are zero) as BF16, canonical layout
+    for (int i = tid; i < a.n_pad * kK; i += kThreads) {
+        const int n = i / kK, k = i - n * kK;
+        const float v = n < a.N ? a.W[(size_t)n * kK + k] : 0.f;
+        Wm[core_off(n, k)] = __float2bfloat16_rn(v);
+    }
+    if (a.first)
+        for (int i = tid; i < kMlpHidden * (kMlpIn + 1); i += kThreads)
+            w1[i] = i < kMlpHidden * kMlpIn ? a.W1[i] : a.b1[i - kMlpHidden * kMlpIn];
+    fence_proxy_async_smem();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = instr_desc_bf16(kRows, (uint32_t)a.n_pad);
+    const uint32_t a_base = smem_addr(Am), w_base = smem_addr(Wm);
+
+    const int64_t n_tiles = (a.n_rows + kRows - 1) / kRows;
+    uint32_t phase = 0;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int64_t r0 = t * kRows;
+        // ---- A operand: relu(previous layer) as BF16 ----
+        if (a.first) {
+            // row tid: features, then relu(W1 x + b1)
+            const int64_t r = r0 + tid;
+            float sa = 0.f, ca = 0.f, se = 0.f, ce = 0.f, ear = 0.f;
+            if (r < a.n_rows) {
+                const float *d = a.dirs + r * 3;
+                sincosf(d[0], &sa, &ca);
+                sincosf(d[1], &se, &ce);
+                ear = d[2];
+            }
+            const float x[kMlpIn] = {sa, ca, se, ce, ear};
+            for (int kc = 0; kc < kKc; ++kc) {
+                uint32_t h[4];
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                    float z2[2];
+#pragma unroll
+                    for (int jj = 0; jj < 2; ++jj) {
+                        const int n = kc * 8 + j + jj;
+                        float z = w1[kMlpHidden * kMlpIn + n];
+#pragma unroll
+                        for (int q = 0; q < kMlpIn; ++q) z = fmaf(w1[n * kMlpIn + q], x[q], z);
+                        z2[jj] = r < a.n_rows ? fmaxf(z, 0.f) : 0.f;
+                    }
+                    h[j / 2] = pack_bf16(z2[0], z2[1]);
+                }
+                *reinterpret_cast<uint4 *>(Am + core_off(tid, kc * 8)) = make_uint4(h[0], h[1], h[2], h[3]);
+            }
+        } else {
+            for (int i = tid; i < kRows * kKc; i += kThreads) {
+                const int row = i / kKc, kc = i - row * kKc;
+                const int64_t r = r0 + row;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (r < a.n_rows) v = *reinterpret_cast<const uint4 *>(a.in + r * kK + kc * 8);
+                *reinterpret_cast<uint4 *>(Am + core_off(row, kc * 8)) = v;
+            }
+        }
+        fence_proxy_async_smem();
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+#pragma unroll 1
+            for (int ks = 0; ks < kK / 16; ++ks) {
+                const uint64_t ad = smem_desc(a_base + ks * 256, 128, kKc * 128);
+                const uint64_t bd = smem_desc(w_base + ks * 256, 128, kKc * 128);
+                const uint32_t acc = ks > 0 ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_addr(bar))
+                : "memory");
+        }
+        const bool ok = mbar_wait_bounded(smem_addr(bar), phase, abort_flag, a.status);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        phase ^= 1;
+        // ---- epilogue: lane = row ----
+        if (ok) {
+            const int row = warp * 32 + lane;
+            const int64_t r = r0 + row;
+            for (int c0 = 0; c0 < a.n_pad; c0 += 32) {
+                uint32_t v[32];
+                tm_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+                if (r >= a.n_rows) continue;
+                if (a.last) {
+                    float *o = a.out + r * a.N;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (c0 + j < a.N) o[c0 + j] = softplus_f(__uint_as_float(v[j]) + a.b[c0 + j]);
+                } else {
+                    uint32_t h[16];
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2)
+                        h[j / 2] = pack_bf16(fmaxf(__uint_as_float(v[j]) + a.b[c0 + j], 0.f),
+                                             fmaxf(__uint_as_float(v[j + 1]) + a.b[c0 + j + 1], 0.f));
+                    uint4 *o = reinterpret_cast<uint4 *>(a.hout + r * kK + c0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) o[j] = make_uint4(h[4 * j], h[4 * j + 1], h[4 * j + 2], h[4 * j + 3]);
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();   // A and the accumulator are reused by the next tile
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) break;
+    }
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                     : "memory");
+}
+
+}  // namespace
+
+size_t mlp_tc_smem_bytes(int n_pad)
+{
+    return (size_t)(n_pad + kRows) * kK * 2 + 16 + (size_t)kMlpHidden * (kMlpIn + 1) * 4;
+}
+
+cudaError_t launch_mlp_layer_tc(const MlpTcArgs &a, int grid, cudaStream_t st)
+{
+    if (a.n_pad < 16 || a.n_pad > 256 || a.n_pad % 16 || a.N > a.n_pad) return cudaErrorInvalidValue;
+    const size_t smem = mlp_tc_smem_bytes(a.n_pad);
+    cudaError_t e = cudaFuncSetAttribute(mlp_layer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    mlp_layer_tc_kernel<<<grid, kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace hrir

@@ -10,9 +10,11 @@ namespace {
 
 // ---- top-K: one warp per row ---------------------------------------------------------------
 // Keeps the k largest strictly positive entries (ties -> smaller index), emitted in ascending
-// index order, padded with (0, 0).  Lane l holds the contiguous slice [l*per, (l+1)*per).
+// index order, padded with (0, 0).  Lane l holds the contiguous slice [l*per, (l+1)*per) in
+// MAXPER registers (the smallest of 8, 16, 32, 64 that holds per = ceil(refl_len / 32)).
 constexpr int kTopkMaxPer = 64;  // refl_len <= 32 * 64 = 2048
 
+template <int MAXPER>
 __global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, int n_rows,
                                                    int refl_len, int k, uint16_t *__restrict__ idx,
                                                    float *__restrict__ w, uint8_t *__restrict__ nnz)
@@ -23,9 +25,9 @@ __global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, 
     const int per = (refl_len + 31) / 32;
     const int j0 = lane * per;
     const float *gr = g + (size_t)row * refl_len;
-    float v[kTopkMaxPer];
+    float v[MAXPER];
 #pragma unroll
-    for (int j = 0; j < kTopkMaxPer; ++j) {
+    for (int j = 0; j < MAXPER; ++j) {
         const int gi = j0 + j;
         v[j] = (j < per && gi < refl_len) ? gr[gi] : 0.0f;  // 0 is never selected
     }
@@ -35,7 +37,7 @@ __global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, 
         float bv = 0.f;
         int bi = INT_MAX;
 #pragma unroll
-        for (int j = 0; j < kTopkMaxPer; ++j) {
+        for (int j = 0; j < MAXPER; ++j) {
             const bool ok = !((taken >> j) & 1ull) && (v[j] > 0.f);
             if (ok && (bi == INT_MAX || v[j] > bv)) {
                 bv = v[j];
@@ -68,7 +70,7 @@ __global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, 
     float *rw = w + (size_t)row * k;
     int o = before;
 #pragma unroll
-    for (int j = 0; j < kTopkMaxPer; ++j) {
+    for (int j = 0; j < MAXPER; ++j) {
         if ((taken >> j) & 1ull) {
             ri[o] = (uint16_t)(j0 + j);
             rw[o] = v[j];
@@ -166,7 +168,12 @@ cudaError_t launch_topk(const float *g, int n_rows, int refl_len, int k, uint16_
 {
     if (n_rows <= 0) return cudaSuccess;
     if (refl_len > 32 * kTopkMaxPer) return cudaErrorInvalidValue;
-    topk_kernel<<<(n_rows + 3) / 4, 128, 0, st>>>(g, n_rows, refl_len, k, idx, w, nnz);
+    const int per = (refl_len + 31) / 32;
+    const unsigned blocks = (unsigned)((n_rows + 3) / 4);
+    if (per <= 8) topk_kernel<8><<<blocks, 128, 0, st>>>(g, n_rows, refl_len, k, idx, w, nnz);
+    else if (per <= 16) topk_kernel<16><<<blocks, 128, 0, st>>>(g, n_rows, refl_len, k, idx, w, nnz);
+    else if (per <= 32) topk_kernel<32><<<blocks, 128, 0, st>>>(g, n_rows, refl_len, k, idx, w, nnz);
+    else topk_kernel<64><<<blocks, 128, 0, st>>>(g, n_rows, refl_len, k, idx, w, nnz);
     return cudaGetLastError();
 }
 

@@ -52,6 +52,7 @@ SIGNATURES = {
     "hrir_mlp_param_count": ([_i], _i64),
     "hrir_mlp_act_stride": ([_i], _i64),
     "hrir_mlp_forward": ([_vp, _i64, _vp, _i, _vp, _vp, _vp, _vp], _i),
+    "hrir_mlp_forward_bf16": ([_vp, _i64, _vp, _i, _vp, _vp, _vp], _i),
     "hrir_mlp_backward": ([_vp, _i64, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "hrir_mlp_adam": ([_vp, _i64, _vp, _vp, _vp, _vp, _i, ctypes.c_float, ctypes.c_float,
                        ctypes.c_float, ctypes.c_float, _vp], _i),
@@ -352,6 +353,20 @@ def hrir_mlp_forward(ctx, dirs, params, refl_len: int, out=None, acts=None, stre
         ctx, n, _f32_cuda(dirs, (n, 3)), refl_len,
         _f32_cuda(params, (hrir_mlp_param_count(refl_len),)), _f32_cuda(out, (n, refl_len)),
         _f32_cuda(acts, (n, hrir_mlp_act_stride(refl_len))) if acts is not None else None,
+        _stream_handle(stream))
+    _check(ctx, rc)
+    return out
+
+
+def hrir_mlp_forward_bf16(ctx, dirs, params, refl_len: int, out=None, stream=None):
+    """Tensor-core (BF16) inference of the network: returns out [n][refl_len] (CUDA)."""
+    import torch
+    n = dirs.shape[0]
+    if out is None:
+        out = torch.empty((n, refl_len), dtype=torch.float32, device=dirs.device)
+    rc = load_library().hrir_mlp_forward_bf16(
+        ctx, n, _f32_cuda(dirs, (n, 3)), refl_len,
+        _f32_cuda(params, (hrir_mlp_param_count(refl_len),)), _f32_cuda(out, (n, refl_len)),
         _stream_handle(stream))
     _check(ctx, rc)
     return out

@@ -105,14 +105,17 @@ class FilterNet:
         self.step_count += steps
         return losses.cpu().numpy()
 
-    def filters(self, rows, out=None):
-        """g [n][Lg] (CUDA) for input rows [n][3]."""
+    def filters(self, rows, out=None, precision: str = "fp32"):
+        """g [n][Lg] (CUDA) for input rows [n][3]; precision "fp32" (the training kernels) or
+        "bf16" (tensor-core inference)."""
         import torch
         rows = rows if torch.is_tensor(rows) else torch.as_tensor(np.asarray(rows, np.float32))
-        return hrir.hrir_mlp_forward(self.r.ctx, rows.cuda().float().contiguous(), self.params,
-                                     self.refl_len, out=out)
+        rows = rows.cuda().float().contiguous()
+        if precision == "bf16":
+            return hrir.hrir_mlp_forward_bf16(self.r.ctx, rows, self.params, self.refl_len, out=out)
+        return hrir.hrir_mlp_forward(self.r.ctx, rows, self.params, self.refl_len, out=out)
 
-    def tap_tables(self, az, el, k: int):
+    def tap_tables(self, az, el, k: int, precision: str = "bf16"):
         """Per-(source, segment) tap tables for hrir_render_moving from directions az, el
         [S][n_seg] (radians): network filters for both ears, then top-k.  Returns CUDA
         (idx [S][n_seg][2][k], w, nnz [S][n_seg][2])."""
@@ -120,7 +123,7 @@ class FilterNet:
         az = np.asarray(az)
         S, n_seg = az.shape
         rows = torch.as_tensor(direction_rows(az, el)).cuda()
-        g = self.filters(rows).view(S, n_seg, 2, self.refl_len)
+        g = self.filters(rows, precision=precision).view(S, n_seg, 2, self.refl_len)
         return self.r.topk_pack(g, k)
 
 

@@ -78,6 +78,31 @@ def test_mlp_forward_backward_match_oracle(rend, B, refl_len):
     np.testing.assert_array_equal(g2, g.astype(np.float32))
 
 
+@pytest.mark.parametrize("n,refl_len", [(1000, 200), (129, 33), (1, 256), (300, 256)])
+def test_tensor_core_inference_matches_fp32_forward(rend, n, refl_len):
+    """BF16 tensor-core inference against the FP32 kernels (and the FP64 oracle): the
+    weights and activations are rounded to BF16 (8-bit significand), so the filters agree to
+    a few parts in a thousand of the largest tap."""
+    from paper_1502_03162_gb300 import hrir
+    rng = np.random.default_rng(n + refl_len)
+    rows = _rows(rng, n)
+    p = _params(rng, refl_len)
+    rows_d = torch.from_numpy(rows).cuda()
+    p_d = torch.from_numpy(p).cuda()
+    g32 = hrir.hrir_mlp_forward(rend.ctx, rows_d, p_d, refl_len).cpu().numpy().astype(np.float64)
+    g16 = hrir.hrir_mlp_forward_bf16(rend.ctx, rows_d, p_d, refl_len).cpu().numpy().astype(np.float64)
+    assert rend.sync() == 0
+    X = omlp.features(rows[:, 0].astype(np.float64), rows[:, 1].astype(np.float64),
+                      rows[:, 2].astype(np.float64))
+    g_ref, _ = omlp.forward(p.astype(np.float64), X, refl_len)
+    scale = np.max(np.abs(g_ref))
+    assert np.all(np.isfinite(g16)) and np.all(g16 > 0)
+    assert np.max(np.abs(g16 - g_ref)) <= 2e-2 * scale
+    assert np.max(np.abs(g16 - g32)) <= 2e-2 * scale
+    # the error is BF16 rounding, not a layout fault: it is far below the filters' spread
+    assert np.sqrt(np.mean((g16 - g_ref) ** 2)) <= 5e-3 * np.sqrt(np.mean(g_ref ** 2)) + 1e-7
+
+
 def test_adam_matches_oracle(rend):
     from paper_1502_03162_gb300 import hrir
     rng = np.random.default_rng(11)

@@ -27,7 +27,7 @@ def _dev(a, dtype=None):
 
 
 # ------------------------------------------------------------------------------- top-K pack
-@pytest.mark.parametrize("refl_len", [200, 33, 2048])
+@pytest.mark.parametrize("refl_len", [200, 33, 500, 1000, 2048])
 def test_topk_pack_bit_exact(rend, refl_len):
     rng = np.random.default_rng(100 + refl_len)
     G = synth.reflection_bank(rng, 64, n_refl=min(60, refl_len), refl_len=refl_len)
