@@ -187,6 +187,8 @@ cudaError_t launch_mlp_layer_tc(const MlpTcArgs &a, int grid, cudaStream_t st);
 
 // ---- moving sources: per-segment filters with a linear crossfade ---------------------------
 constexpr int kMovTile = 1024;   // outputs per (tile, source) unit
+constexpr int kMovMaxHalo = 1024;  // history samples per window (Lg rounded up to 4)
+constexpr int kMovMaxTaps = 1024;  // taps staged per unit: segments x 2 ears x k_max
 struct MovingArgs {
     const float *src;            // [n_src][ld]
     int64_t ld, len;

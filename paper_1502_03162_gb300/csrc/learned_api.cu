@@ -330,7 +330,9 @@ int hrir_render_moving(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, co
     a.slots = slots;
     a.status = ctx->d_status;
     const size_t smem = moving_smem_bytes(a.halo, a.n_js, k_max);
-    if (smem > 227 * 1024) return fail(ctx, HRIR_EINVAL, "filters too long for the shared-memory window");
+    if (a.halo > kMovMaxHalo || (int64_t)a.n_js * 2 * k_max > kMovMaxTaps)
+        return fail(ctx, HRIR_EINVAL, "reflection filters too long (Lg <= %d) or too many taps for "
+                    "the segment length (%d segments x 2 ears x k_max <= %d)", kMovMaxHalo, a.n_js, kMovMaxTaps);
     {
         KernelTimer kt(ctx, HRIR_K_MOVING, st);
         HRIR_CUDA_TRY(ctx, launch_moving_mix(a, (int)part.P, smem, st));

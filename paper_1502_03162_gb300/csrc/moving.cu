@@ -13,8 +13,10 @@
 // tile): a CTA takes (output tile of 1024, source) units from a balanced contiguous range;
 // the tile's source window is staged as four copies shifted by 0..3 samples, so that the 4
 // consecutive samples y[n - i .. n - i + 3] a thread needs for its outputs n..n+3 are one
-// aligned 16-byte load from the copy (-i) mod 4 for every tap i.  A warp covers 128 outputs
-// inside one segment (seg_len is a multiple of 128), so its taps are warp-uniform broadcasts.
+// aligned 16-byte load from the copy (-i) mod 4 for every tap i.  The next unit's window and
+// taps are loaded into registers while the current unit's taps run (3 CTAs per SM).  A warp
+// covers 128 outputs inside one segment (seg_len is a multiple of 128), so its taps are
+// warp-uniform broadcasts.
 // Runs of <= 64 sources accumulate in registers and are flushed to partial slots.
 #include "kernels.h"
 
@@ -27,10 +29,34 @@ constexpr int kPer = 4;                        // outputs per thread
 constexpr int kTile = kThreads * kPer;         // 1024
 static_assert(kTile == kMovTile, "tile");
 
-__global__ void __launch_bounds__(kThreads) moving_mix_kernel(const MovingArgs a)
+// Window chunks (4 samples) a thread prefetches per unit: ceil((halo + kTile) / 4 / kThreads).
+constexpr int kMaxChunks = 2;                  // halo <= 1024
+constexpr int kMaxTapsPerThread = 4;           // n_js * 2 * k_max <= kThreads * 4
+
+// Loads of one unit kept in registers until the previous unit's taps are done.
+struct Prefetch {
+    float4 v0[kMaxChunks], v1[kMaxChunks];     // chunk q and q + 1 of the window
+    int2 tap[kMaxTapsPerThread];
+    int cnt;
+};
+
+__device__ __forceinline__ float4 chunk(const float *ys, int64_t p, int64_t len)
+{
+    // samples p .. p + 3 (p a multiple of 4), zero outside [0, len)
+    if (p >= 0 && p + 4 <= len) return __ldg(reinterpret_cast<const float4 *>(ys + p));
+    float4 v;
+    v.x = (p >= 0 && p < len) ? __ldg(ys + p) : 0.f;
+    v.y = (p + 1 >= 0 && p + 1 < len) ? __ldg(ys + p + 1) : 0.f;
+    v.z = (p + 2 >= 0 && p + 2 < len) ? __ldg(ys + p + 2) : 0.f;
+    v.w = (p + 3 >= 0 && p + 3 < len) ? __ldg(ys + p + 3) : 0.f;
+    return v;
+}
+
+__global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int win = a.halo + kTile;            // samples per shifted copy
+    const int win = a.halo + kTile;            // samples per shifted copy (multiple of 4)
+    const int n_chunks = win / 4;
     float *Y = reinterpret_cast<float *>(smem);                 // [4][win]
     int2 *taps = reinterpret_cast<int2 *>(Y + 4 * win);         // [n_js][2][k_max]
     int *cnt = reinterpret_cast<int *>(taps + a.n_js * 2 * a.k_max);  // [n_js][2]
@@ -38,66 +64,106 @@ __global__ void __launch_bounds__(kThreads) moving_mix_kernel(const MovingArgs a
     const int tid = threadIdx.x, warp = tid >> 5;
     const int64_t u_begin = a.part.first(blockIdx.x);
     const int64_t u_end = a.part.first(blockIdx.x + 1);
+    const int n_tap = a.n_js * 2 * a.k_max;
+
+    // ---- global loads of unit u into registers ----
+    auto fetch = [&](int64_t u, Prefetch &pf) {
+        const int t = (int)(u / a.n_src);
+        const int s = (int)(u - (int64_t)t * a.n_src);
+        const int64_t t0 = (int64_t)t * kTile;
+        const int64_t wb = t0 - a.halo;
+        const float *ys = a.src + (int64_t)s * a.ld;
+#pragma unroll
+        for (int c = 0; c < kMaxChunks; ++c) {
+            const int q = tid + c * kThreads;
+            if (q < n_chunks) {
+                pf.v0[c] = chunk(ys, wb + 4 * q, a.len);
+                pf.v1[c] = chunk(ys, wb + 4 * q + 4, a.len);
+            }
+        }
+        int64_t jl = t0 / a.seg_len - 1;
+        jl = jl < 0 ? 0 : jl;
+        const int j_lo = (int)(jl < a.n_seg - 1 ? jl : a.n_seg - 1);
+#pragma unroll
+        for (int c = 0; c < kMaxTapsPerThread; ++c) {
+            const int i = tid + c * kThreads;
+            if (i < n_tap) {
+                const int jj = i / (2 * a.k_max);
+                const int ek = i - jj * 2 * a.k_max;
+                const int j = min(j_lo + jj, a.n_seg - 1);
+                const int64_t row = ((int64_t)s * a.n_seg + j) * 2 * a.k_max + ek;
+                pf.tap[c] = make_int2((int)a.tap_idx[row], __float_as_int(a.tap_w[row]));
+            }
+        }
+        if (tid < a.n_js * 2) {
+            const int j = min(j_lo + (tid >> 1), a.n_seg - 1);
+            pf.cnt = a.tap_nnz[((int64_t)s * a.n_seg + j) * 2 + (tid & 1)];
+        }
+    };
+    // ---- registers -> shared memory: Y[c][q] = y[wb + q + c]; taps checked ----
+    // (a tap index >= Lg or a count > k_max is ignored and flagged: the window only holds
+    // Lg - 1 samples of history)
+    auto stage = [&](const Prefetch &pf) {
+#pragma unroll
+        for (int c = 0; c < kMaxChunks; ++c) {
+            const int q = tid + c * kThreads;
+            if (q < n_chunks) {
+                const float4 x = pf.v0[c], y = pf.v1[c];
+                float4 *d = reinterpret_cast<float4 *>(Y) + q;
+                d[0] = x;
+                d[n_chunks] = make_float4(x.y, x.z, x.w, y.x);
+                d[2 * n_chunks] = make_float4(x.z, x.w, y.x, y.y);
+                d[3 * n_chunks] = make_float4(x.w, y.x, y.y, y.z);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kMaxTapsPerThread; ++c) {
+            const int i = tid + c * kThreads;
+            if (i < n_tap) {
+                int2 tp = pf.tap[c];
+                if (tp.x >= a.refl_len) {
+                    atomicOr(a.status, DEV_BAD_TAP);
+                    tp = make_int2(0, 0);
+                }
+                taps[i] = tp;
+            }
+        }
+        if (tid < a.n_js * 2) {
+            int n = pf.cnt;
+            if (n > a.k_max) {
+                atomicOr(a.status, DEV_BAD_TAP);
+                n = a.k_max;
+            }
+            cnt[tid] = n;
+        }
+    };
+
     float zr[2][kPer];
 #pragma unroll
     for (int e = 0; e < 2; ++e)
 #pragma unroll
         for (int r = 0; r < kPer; ++r) zr[e][r] = 0.f;
     int cur_t = -1, slot = 0, run_n = 0;
+    Prefetch pf;
+    pf.cnt = 0;
+    if (u_begin < u_end) fetch(u_begin, pf);
 
     for (int64_t u = u_begin; u < u_end; ++u) {
         const int t = (int)(u / a.n_src);
-        const int s = (int)(u - (int64_t)t * a.n_src);
         if (t != cur_t) {
             cur_t = t;
             slot = a.part.slot_base(blockIdx.x, t);
             run_n = 0;
         }
         const int64_t t0 = (int64_t)t * kTile;
-        const int64_t wb = t0 - a.halo;
-        // ---- stage the window: Y[c][q] = y[wb + q + c], zero outside [0, len) ----
-        const float *ys = a.src + (int64_t)s * a.ld;
-        for (int q = tid; q < win + 3; q += kThreads) {
-            const int64_t p = wb + q;
-            const float v = (p >= 0 && p < a.len) ? __ldg(ys + p) : 0.f;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int qq = q - c;
-                if (qq >= 0 && qq < win) Y[c * win + qq] = v;
-            }
-        }
-        // ---- stage the taps of the segments this tile touches (and the one before) ----
-        // (a tap index >= Lg or a count > k_max is ignored and flagged: the window only
-        // holds Lg - 1 samples of history)
+        __syncthreads();                       // the previous unit's reads of Y and taps are done
+        stage(pf);
+        __syncthreads();
+        if (u + 1 < u_end) fetch(u + 1, pf);   // in flight during this unit's taps
+
         int64_t jl = t0 / a.seg_len - 1;
         jl = jl < 0 ? 0 : jl;
         const int j_lo = (int)(jl < a.n_seg - 1 ? jl : a.n_seg - 1);
-        for (int i = tid; i < a.n_js * 2 * a.k_max; i += kThreads) {
-            const int jj = i / (2 * a.k_max);
-            const int ek = i - jj * 2 * a.k_max;
-            const int j = min(j_lo + jj, a.n_seg - 1);
-            const int64_t row = ((int64_t)s * a.n_seg + j) * 2 * a.k_max + ek;
-            int idx = (int)a.tap_idx[row];
-            float w = a.tap_w[row];
-            if (idx >= a.refl_len) {
-                atomicOr(a.status, DEV_BAD_TAP);
-                idx = 0;
-                w = 0.f;
-            }
-            taps[i] = make_int2(idx, __float_as_int(w));
-        }
-        for (int i = tid; i < a.n_js * 2; i += kThreads) {
-            const int jj = i >> 1;
-            const int j = min(j_lo + jj, a.n_seg - 1);
-            int n = a.tap_nnz[((int64_t)s * a.n_seg + j) * 2 + (i & 1)];
-            if (n > a.k_max) {
-                atomicOr(a.status, DEV_BAD_TAP);
-                n = a.k_max;
-            }
-            cnt[i] = n;
-        }
-        __syncthreads();
-
         // ---- this warp's segment and crossfade ----
         const int64_t nw = t0 + 128 * warp;
         const int64_t jw = nw / a.seg_len;
@@ -110,11 +176,12 @@ __global__ void __launch_bounds__(kThreads) moving_mix_kernel(const MovingArgs a
         for (int e = 0; e < 2; ++e)
 #pragma unroll
             for (int r = 0; r < kPer; ++r) cur[e][r] = prv[e][r] = 0.f;
+        const int jc = jcur - j_lo;
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const int jc = jcur - j_lo;
             const int2 *tc = taps + (jc * 2 + e) * a.k_max;
             const int nc = cnt[jc * 2 + e];
+#pragma unroll 2
             for (int k = 0; k < nc; ++k) {
                 const int2 tp = tc[k];
                 const int c = (-tp.x) & 3;
@@ -129,6 +196,7 @@ __global__ void __launch_bounds__(kThreads) moving_mix_kernel(const MovingArgs a
                 const int jp = jc - 1;
                 const int2 *tq = taps + (jp * 2 + e) * a.k_max;
                 const int np = cnt[jp * 2 + e];
+#pragma unroll 2
                 for (int k = 0; k < np; ++k) {
                     const int2 tp = tq[k];
                     const int c = (-tp.x) & 3;
@@ -148,7 +216,6 @@ __global__ void __launch_bounds__(kThreads) moving_mix_kernel(const MovingArgs a
 #pragma unroll
             for (int e = 0; e < 2; ++e) zr[e][r] += fade ? fmaf(al, cur[e][r] - prv[e][r], prv[e][r]) : cur[e][r];
         }
-        __syncthreads();
 
         ++run_n;
         const bool tile_end = (u + 1 == u_end) || ((u + 1) / a.n_src != t);
