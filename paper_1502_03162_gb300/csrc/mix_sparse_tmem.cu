@@ -21,7 +21,8 @@
 // an AND vote, so that both warps leave together on a timeout) hands the buffers over.
 // A ring of up to 6 shared-memory stages holds each unit's source tile (tensor TMA, 256-sample
 // halo, hardware zero fill outside [0, len)) and the direction's tap record (bulk copy): the
-// last of the 8 warps to release a stage refills it at once with the unit `stages` ahead.  Work is a persistent balanced range of units per CTA; register accumulators are
+// last of the 8 warps to release a stage refills it at once with the unit `stages` ahead.
+// Work is a persistent balanced range of units per CTA; register accumulators are
 // flushed every <= 64 sources into partial slots that the reduction sums in a fixed order.
 // All waits are bounded.
 #include <cuda_bf16.h>
@@ -248,23 +249,44 @@ __device__ __forceinline__ void apply_taps(float (&acc)[R], uint32_t tw, const i
 // Issue the TMA loads of unit u into a pipeline stage (all lanes of the producer warp).
 template <typename T>
 __device__ __forceinline__ void issue_unit(const CUtensorMap *tmap, const CUtensorMap *tmap3,
-                                           const MixArgs &a, int64_t u, int d, T *ybuf,
+                                           const MixArgs &a, int t, int s, int d, T *ybuf,
                                            unsigned char *rbuf, uint32_t full_bar, int lane)
 {
-    const int t = (int)(u / a.n_src);
-    const int s = (int)(u - (int64_t)t * a.n_src);
     const int x0 = t * kTile - a.halo;
     const int n_box = a.buf_elems / kMixBox;
-    if (lane == 0)
-        mbar_arrive_expect_tx(full_bar, (uint32_t)(a.buf_elems * sizeof(T) + a.rec_bytes));
-    __syncwarp();
     // The tile starts on a row of the 3-D view (x0 % kMixBox == 0); when every row it covers
     // is a full row of the source, one request loads it (rows before the source read as
-    // zeros).  Tiles that reach the ragged last row use one-row boxes of the 2-D map.
+    // zeros).  A tile reaching past the last full row (the last tile of every source): one
+    // bulk copy of its full rows, one 2-D box for the ragged row (zero fill past len), and
+    // zeros stored here for the rows past the source, before the arrive that publishes them.
+    // Tiny sources whose first tile is also ragged use one-row boxes of the 2-D map.
     const int r0 = x0 >= 0 ? x0 / kMixBox : -((-x0 + kMixBox - 1) / kMixBox);
     if (r0 + n_box <= a.full_rows) {
-        if (lane == 0) tma_load_3d(smem_addr(ybuf), tmap3, 0, r0, s, full_bar);
+        if (lane == 0) {
+            mbar_arrive_expect_tx(full_bar, (uint32_t)(a.buf_elems * sizeof(T) + a.rec_bytes));
+            tma_load_3d(smem_addr(ybuf), tmap3, 0, r0, s, full_bar);
+        }
+    } else if (r0 >= 0) {
+        // r0 <= full_rows: the last tile's window starts before len
+        const int n_full = a.full_rows - r0 > 0 ? a.full_rows - r0 : 0;   // < n_box
+        const bool ragged = r0 <= a.full_rows && (int64_t)a.full_rows * kMixBox < a.len;
+        const int n_data = n_full + (ragged ? 1 : 0);
+        for (int i = n_data * kMixBox + lane; i < a.buf_elems; i += 32) ybuf[i] = T(0.f);
+        fence_proxy_async_smem();   // these stores before any later TMA write to the stage
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive_expect_tx(full_bar, (uint32_t)(n_data * kMixBox * sizeof(T) + a.rec_bytes));
+            if (n_full > 0)
+                tma_load_1d(smem_addr(ybuf), static_cast<const T *>(a.src) + (int64_t)s * a.ld + x0,
+                            (uint32_t)(n_full * kMixBox * sizeof(T)), full_bar);
+            if (ragged)
+                tma_load_2d(smem_addr(ybuf + n_full * kMixBox), tmap, a.full_rows * kMixBox, s,
+                            full_bar);
+        }
     } else {
+        if (lane == 0)
+            mbar_arrive_expect_tx(full_bar, (uint32_t)(a.buf_elems * sizeof(T) + a.rec_bytes));
+        __syncwarp();
         for (int b = lane; b < n_box; b += 32)
             tma_load_2d(smem_addr(ybuf + b * kMixBox), tmap, x0 + b * kMixBox, s, full_bar);
     }
@@ -273,11 +295,19 @@ __device__ __forceinline__ void issue_unit(const CUtensorMap *tmap, const CUtens
                     full_bar);
 }
 
-// Raw direction id of unit u.
-__device__ __forceinline__ int raw_dir(const MixArgs &a, int64_t u)
-{
-    return __ldg(a.dir + (int)(u % a.n_src));
-}
+// Position (output tile t, source s) of a unit; units are ordered tile-major.  Advanced by
+// small steps without a division (n <= the ring depth).
+struct UnitPos {
+    int t, s;
+    __device__ __forceinline__ void advance(int n, int n_src)
+    {
+        s += n;
+        while (s >= n_src) {
+            s -= n_src;
+            ++t;
+        }
+    }
+};
 
 // Record index for a direction id: the silent record for an id out of range.
 __device__ __forceinline__ int checked_dir(const MixArgs &a, int d, int lane)
@@ -336,25 +366,33 @@ __global__ void __launch_bounds__(NW * 32, 1)
 
     const int64_t u_begin = a.part.first(blockIdx.x);
     const int64_t u_end = a.part.first(blockIdx.x + 1);
-    const int64_t n_units = u_end - u_begin;
+    const int n_units = (int)(u_end - u_begin);
+    UnitPos pos0;                                   // position of this CTA's first unit
+    pos0.t = (int)(u_begin / a.n_src);
+    pos0.s = (int)(u_begin - (int64_t)pos0.t * a.n_src);
     // directions of this CTA's first kMixDirCache units, staged once
-    const int n_cached = (int)(n_units < kMixDirCache ? n_units : kMixDirCache);
-    for (int i = threadIdx.x; i < n_cached; i += blockDim.x) dircache[i] = raw_dir(a, u_begin + i);
+    const int n_cached = n_units < kMixDirCache ? n_units : kMixDirCache;
+    {
+        UnitPos p = pos0;
+        p.advance(threadIdx.x, a.n_src);
+        for (int i = threadIdx.x; i < n_cached; i += blockDim.x) {
+            dircache[i] = __ldg(a.dir + p.s);
+            p.advance(blockDim.x, a.n_src);
+        }
+    }
     __syncthreads();
 
-    // Issue unit k (local index) into its stage (all lanes of the calling warp).
-    auto issue = [&](int64_t k) {
-        const int st = (int)(k % stages);
-        const int d = checked_dir(a, k < n_cached ? dircache[k] : raw_dir(a, u_begin + k), lane);
-        issue_unit<T>(&tmap, &tmap3, a, u_begin + k, d, ybuf + (size_t)st * a.buf_elems,
+    // Issue unit k (local index, at position p) into stage st (all lanes of the calling warp).
+    auto issue = [&](int k, UnitPos p, int st) {
+        const int d = checked_dir(a, k < n_cached ? dircache[k] : __ldg(a.dir + p.s), lane);
+        issue_unit<T>(&tmap, &tmap3, a, p.t, p.s, d, ybuf + (size_t)st * a.buf_elems,
                       rbuf + (size_t)st * a.rec_bytes, smem_addr(&bars[st]), lane);
-        if (lane == 0) last_issued[st] = (int)k;
+        if (lane == 0) last_issued[st] = k;
     };
-    // A warp is done with unit k's stage: arrive on its empty barrier; the last of the NW
-    // warps to arrive refills the stage with unit k + stages at once.  Returns false on a
-    // timeout.
-    auto release = [&](int64_t k) {
-        const int st = (int)(k % stages);
+    // A warp is done with unit k (at position p, stage st, phase parity ph): arrive on the
+    // stage's empty barrier; the last of the NW warps to arrive refills the stage with unit
+    // k + stages at once.  Returns false on a timeout.
+    auto release = [&](int k, UnitPos p, int st, uint32_t ph) {
         __syncwarp();
         int last = 0;
         if (lane == 0) {
@@ -367,10 +405,10 @@ __global__ void __launch_bounds__(NW * 32, 1)
         if (k + stages >= n_units) return true;
         // every warp has arrived: the phase completes (its acquire orders their reads of the
         // stage before the copy that overwrites it)
-        if (!mbar_wait_bounded(smem_addr(&bars[stages + st]), (uint32_t)((k / stages) & 1),
-                               abort_flag, a.status))
+        if (!mbar_wait_bounded(smem_addr(&bars[stages + st]), ph, abort_flag, a.status))
             return false;
-        issue(k + stages);
+        p.advance(stages, a.n_src);
+        issue(k + stages, p, st);
         return true;
     };
 
@@ -380,71 +418,73 @@ __global__ void __launch_bounds__(NW * 32, 1)
         const uint32_t tq = tmem_base + ((uint32_t)(32 * q) << 16);
         const int lane_off = (q * 32 + lane) * R;
         const int n_seg = a.nseg;
-        const int64_t n_steps = n_units * n_seg;
+        const int64_t n_steps = (int64_t)n_units * n_seg;
         float acc[R];
 #pragma unroll
         for (int i = 0; i < R; ++i) acc[i] = 0.f;
-        int cur_t = -1, slot = 0, run_n = 0;
+        int slot = a.part.slot_base(blockIdx.x, pos0.t), run_n = 0;
 
-        // the window of a step (unit k, segment s) for this warp's half
-        auto window_src = [&](int64_t k, int s) {
-            return ybuf + (size_t)(k % stages) * a.buf_elems + a.halo + lane_off - (s + 1) * SW +
-                   kHalf * ear;
+        // the window of a step (stage st, segment seg) for this warp's half
+        auto window_src = [&](int st, int seg) {
+            return ybuf + (size_t)st * a.buf_elems + a.halo + lane_off - (seg + 1) * SW + kHalf * ear;
         };
         // prologue: fill the ring, the first window into buffer 0
-        if (warp == 0)
-            for (int64_t k0 = 0; k0 < n_units && k0 < stages; ++k0) issue(k0);
+        if (warp == 0) {
+            UnitPos p = pos0;
+            for (int k0 = 0; k0 < n_units && k0 < stages; ++k0) {
+                issue(k0, p, k0);
+                p.advance(1, a.n_src);
+            }
+        }
         bool ok = mbar_wait_bounded(smem_addr(&bars[0]), 0u, abort_flag, a.status);
         if (ok) copy_half<T>(window_src(0, 0), tq + (uint32_t)(kHalf * ear));
         tm_wait_st();
         ok = pair_sync_all(q, ok);
 
-        int64_t k = 0;
-        int s = 0, toff = 0;
+        // current step: unit k at position pos, stage st, parity ph; segment seg
+        int k = 0, st = 0, seg = 0, toff = 0;
+        uint32_t ph = 0;
+        UnitPos pos = pos0;
         for (int64_t j = 0; ok && j < n_steps; ++j) {
-            int64_t k1 = k;
-            int s1 = s + 1;
-            if (s1 == n_seg) {
-                s1 = 0;
-                k1 = k + 1;
+            // next step
+            const bool last_seg = seg == n_seg - 1;
+            const int k1 = last_seg ? k + 1 : k;
+            const int seg1 = last_seg ? 0 : seg + 1;
+            int st1 = st;
+            uint32_t ph1 = ph;
+            if (last_seg && ++st1 == stages) {
+                st1 = 0;
+                ph1 ^= 1u;
             }
             const bool have_next = k1 < n_units;
             bool ok_next = true;
-            if (have_next && s1 == 0)
-                ok_next = mbar_wait_bounded(smem_addr(&bars[k1 % stages]),
-                                            (uint32_t)((k1 / stages) & 1), abort_flag, a.status);
+            if (have_next && last_seg)
+                ok_next = mbar_wait_bounded(smem_addr(&bars[st1]), ph1, abort_flag, a.status);
             // the next window's half: the left-ear warp copies it before its taps, the
             // right-ear warp after them, so that on their shared SM sub-partition one warp's
             // copy overlaps the other's FMAs
             const bool copy = have_next && ok_next;
-            const T *nsrc = window_src(copy ? k1 : k, copy ? s1 : s);
+            const T *nsrc = window_src(copy ? st1 : st, copy ? seg1 : seg);
             const uint32_t ndst = tq + (uint32_t)(kCols * ((j + 1) & 1) + kHalf * ear);
             if (copy && ear == 0) copy_half<T>(nsrc, ndst);
-            // taps of this warp's ear in segment s of unit k
-            const unsigned char *rec = rbuf + (size_t)(k % stages) * a.rec_bytes;
-            const int2 c = reinterpret_cast<const int2 *>(rec + 16)[s];
+            // taps of this warp's ear in segment seg of unit k
+            const unsigned char *rec = rbuf + (size_t)st * a.rec_bytes;
+            const int2 c = reinterpret_cast<const int2 *>(rec + 16)[seg];
             const int2 *taps = reinterpret_cast<const int2 *>(rec + 16 + 8 * a.nchunk) + toff +
                                (ear ? c.x : 0);
             apply_taps(acc, tq + (uint32_t)(kCols * (j & 1)), taps, ear ? c.y : c.x);
             toff += c.x + c.y;
-            if (s == n_seg - 1 && !release(k)) ok_next = false;   // last read of unit k's stage
+            if (last_seg && !release(k, pos, st, ph)) ok_next = false;   // last read of unit k's stage
             if (copy && ear == 1) copy_half<T>(nsrc, ndst);
             tm_wait_st();
             ok = pair_sync_all(q, ok_next);
-            if (s == n_seg - 1) {
-                // unit k done: release its stage, flush the run at its end
-                const int64_t u = u_begin + k;
-                const int t = (int)(u / a.n_src);
-                if (t != cur_t) {
-                    cur_t = t;
-                    slot = a.part.slot_base(blockIdx.x, t);
-                    run_n = 0;
-                }
+            if (last_seg) {
+                // unit k done: flush the run at its end
                 ++run_n;
-                const bool tile_end = (u + 1 == u_end) || ((u + 1) / a.n_src != t);
+                const bool tile_end = (k + 1 == n_units) || (pos.s + 1 == a.n_src);
                 if (run_n == a.part.gs || tile_end) {
                     float4 *p = reinterpret_cast<float4 *>(
-                        a.partial + ((size_t)t * a.slots + slot) * 2 * kTile + ear * kTile + lane_off);
+                        a.partial + ((size_t)pos.t * a.slots + slot) * 2 * kTile + ear * kTile + lane_off);
 #pragma unroll
                     for (int i = 0; i < R / 4; ++i)
                         p[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
@@ -454,9 +494,16 @@ __global__ void __launch_bounds__(NW * 32, 1)
                     run_n = 0;
                 }
                 toff = 0;
+                pos.advance(1, a.n_src);
+                if (tile_end && k1 < n_units) {
+                    slot = a.part.slot_base(blockIdx.x, pos.t);   // the next tile's first slot
+                    run_n = 0;
+                }
             }
             k = k1;
-            s = s1;
+            seg = seg1;
+            st = st1;
+            ph = ph1;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
