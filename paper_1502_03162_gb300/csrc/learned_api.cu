@@ -289,7 +289,7 @@ int hrir_render_moving(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, co
     const int64_t out_len = full ? (len > 0 ? len + ctx->hrir_len - 1 : 0) : len;
     if (out_len == 0) return HRIR_OK;
     if (!out || out_ld < out_len) return fail(ctx, HRIR_EINVAL, "out is NULL or out_ld < %lld", (long long)out_len);
-    if (len > (int64_t)1 << 31) return fail(ctx, HRIR_EINVAL, "len must be < 2^31");
+    if (len > ((int64_t)1 << 31) - 8192) return fail(ctx, HRIR_EINVAL, "len must be < 2^31 - 8192");
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HRIR_ECUDA, "cudaSetDevice failed");
     if (n_src == 0) {

@@ -66,12 +66,10 @@ __global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArg
     const int64_t u_end = a.part.first(blockIdx.x + 1);
     const int n_tap = a.n_js * 2 * a.k_max;
 
-    // ---- global loads of unit u into registers ----
-    auto fetch = [&](int64_t u, Prefetch &pf) {
-        const int t = (int)(u / a.n_src);
-        const int s = (int)(u - (int64_t)t * a.n_src);
-        const int64_t t0 = (int64_t)t * kTile;
-        const int64_t wb = t0 - a.halo;
+    // ---- global loads of the unit at (tile t, source s) into registers ----
+    auto fetch = [&](int t, int s, Prefetch &pf) {
+        const int t0 = t * kTile;                  // < 2^31: len < 2^31
+        const int64_t wb = (int64_t)t0 - a.halo;
         const float *ys = a.src + (int64_t)s * a.ld;
 #pragma unroll
         for (int c = 0; c < kMaxChunks; ++c) {
@@ -81,9 +79,9 @@ __global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArg
                 pf.v1[c] = chunk(ys, wb + 4 * q + 4, a.len);
             }
         }
-        int64_t jl = t0 / a.seg_len - 1;
+        int jl = t0 / a.seg_len - 1;
         jl = jl < 0 ? 0 : jl;
-        const int j_lo = (int)(jl < a.n_seg - 1 ? jl : a.n_seg - 1);
+        const int j_lo = jl < a.n_seg - 1 ? jl : a.n_seg - 1;
 #pragma unroll
         for (int c = 0; c < kMaxTapsPerThread; ++c) {
             const int i = tid + c * kThreads;
@@ -143,30 +141,30 @@ __global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArg
     for (int e = 0; e < 2; ++e)
 #pragma unroll
         for (int r = 0; r < kPer; ++r) zr[e][r] = 0.f;
-    int cur_t = -1, slot = 0, run_n = 0;
+    // unit position (tile t, source s), carried without divisions; units are tile-major
+    int t = (int)(u_begin / a.n_src);
+    int s = (int)(u_begin - (int64_t)t * a.n_src);
+    int slot = a.part.slot_base(blockIdx.x, t), run_n = 0;
     Prefetch pf;
     pf.cnt = 0;
-    if (u_begin < u_end) fetch(u_begin, pf);
+    if (u_begin < u_end) fetch(t, s, pf);
 
     for (int64_t u = u_begin; u < u_end; ++u) {
-        const int t = (int)(u / a.n_src);
-        if (t != cur_t) {
-            cur_t = t;
-            slot = a.part.slot_base(blockIdx.x, t);
-            run_n = 0;
-        }
-        const int64_t t0 = (int64_t)t * kTile;
+        const int t0 = t * kTile;
         __syncthreads();                       // the previous unit's reads of Y and taps are done
         stage(pf);
         __syncthreads();
-        if (u + 1 < u_end) fetch(u + 1, pf);   // in flight during this unit's taps
+        if (u + 1 < u_end) {                   // in flight during this unit's taps
+            const bool wrap = s + 1 == a.n_src;
+            fetch(wrap ? t + 1 : t, wrap ? 0 : s + 1, pf);
+        }
 
-        int64_t jl = t0 / a.seg_len - 1;
+        int jl = t0 / a.seg_len - 1;
         jl = jl < 0 ? 0 : jl;
-        const int j_lo = (int)(jl < a.n_seg - 1 ? jl : a.n_seg - 1);
+        const int j_lo = jl < a.n_seg - 1 ? jl : a.n_seg - 1;
         // ---- this warp's segment and crossfade ----
-        const int64_t nw = t0 + 128 * warp;
-        const int64_t jw = nw / a.seg_len;
+        const int nw = t0 + 128 * warp;
+        const int jw = nw / a.seg_len;
         const bool tail = jw >= a.n_seg;
         const int jcur = tail ? a.n_seg - 1 : (int)jw;
         const bool fade = !tail && jw >= 1;
@@ -209,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArg
                 }
             }
         }
-        const int64_t n0 = t0 + kPer * tid;
+        const int n0 = t0 + kPer * tid;
 #pragma unroll
         for (int r = 0; r < kPer; ++r) {
             const float al = fade ? (float)(n0 + r - jw * a.seg_len + 1) / (float)a.seg_len : 1.f;
@@ -218,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArg
         }
 
         ++run_n;
-        const bool tile_end = (u + 1 == u_end) || ((u + 1) / a.n_src != t);
+        const bool tile_end = (u + 1 == u_end) || (s + 1 == a.n_src);
         if (run_n == a.part.gs || tile_end) {
             float *p = a.partial + ((size_t)t * a.slots + slot) * 2 * kTile + kPer * tid;
 #pragma unroll
@@ -229,6 +227,14 @@ __global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArg
             }
             ++slot;
             run_n = 0;
+        }
+        if (++s == a.n_src) {
+            s = 0;
+            ++t;
+            if (u + 1 < u_end) {
+                slot = a.part.slot_base(blockIdx.x, t);   // the next tile's first slot
+                run_n = 0;
+            }
         }
     }
 }
