@@ -254,41 +254,41 @@ __device__ __forceinline__ void issue_unit(const CUtensorMap *tmap, const CUtens
 {
     const int x0 = t * kTile - a.halo;
     const int n_box = a.buf_elems / kMixBox;
-    // The tile starts on a row of the 3-D view (x0 % kMixBox == 0); when every row it covers
-    // is a full row of the source, one request loads it (rows before the source read as
-    // zeros).  A tile reaching past the last full row (the last tile of every source): one
-    // bulk copy of its full rows, one 2-D box for the ragged row (zero fill past len), and
-    // zeros stored here for the rows past the source, before the arrive that publishes them.
-    // Tiny sources whose first tile is also ragged use one-row boxes of the 2-D map.
+    // The tile starts on a row of the 3-D view (x0 % kMixBox == 0).  An interior tile (every
+    // row it covers a full row of the source) is one 3-D request.  A tile at either end of the
+    // source: one bulk copy of the full rows it covers, one 2-D box for the ragged last row (zero
+    // fill past len), and 16-byte zero stores here for the rows before 0 or past the source,
+    // made before the arrive that publishes them.
     const int r0 = x0 >= 0 ? x0 / kMixBox : -((-x0 + kMixBox - 1) / kMixBox);
-    if (r0 + n_box <= a.full_rows) {
+    if (r0 >= 0 && r0 + n_box <= a.full_rows) {
         if (lane == 0) {
             mbar_arrive_expect_tx(full_bar, (uint32_t)(a.buf_elems * sizeof(T) + a.rec_bytes));
             tma_load_3d(smem_addr(ybuf), tmap3, 0, r0, s, full_bar);
         }
-    } else if (r0 >= 0) {
-        // r0 <= full_rows: the last tile's window starts before len
-        const int n_full = a.full_rows - r0 > 0 ? a.full_rows - r0 : 0;   // < n_box
-        const bool ragged = r0 <= a.full_rows && (int64_t)a.full_rows * kMixBox < a.len;
-        const int n_data = n_full + (ragged ? 1 : 0);
-        for (int i = n_data * kMixBox + lane; i < a.buf_elems; i += 32) ybuf[i] = T(0.f);
+    } else {
+        const int lo = r0 < 0 ? (-r0 < n_box ? -r0 : n_box) : 0;         // rows before sample 0
+        int hi = a.full_rows - r0;                                        // end of the full rows
+        hi = hi < lo ? lo : (hi > n_box ? n_box : hi);
+        const int rr = a.full_rows - r0;                                  // the ragged row, if any
+        const bool ragged = (int64_t)a.full_rows * kMixBox < a.len && rr >= lo && rr < n_box;
+        const int end = ragged ? rr + 1 : hi;                             // rows [lo, end) hold data
+        {
+            const int per_row = kMixBox * (int)sizeof(T) / 16;
+            uint4 *z = reinterpret_cast<uint4 *>(ybuf);                    // 16-byte aligned
+            for (int i = lane; i < lo * per_row; i += 32) z[i] = make_uint4(0u, 0u, 0u, 0u);
+            for (int i = end * per_row + lane; i < n_box * per_row; i += 32) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
         fence_proxy_async_smem();   // these stores before any later TMA write to the stage
         __syncwarp();
         if (lane == 0) {
-            mbar_arrive_expect_tx(full_bar, (uint32_t)(n_data * kMixBox * sizeof(T) + a.rec_bytes));
-            if (n_full > 0)
-                tma_load_1d(smem_addr(ybuf), static_cast<const T *>(a.src) + (int64_t)s * a.ld + x0,
-                            (uint32_t)(n_full * kMixBox * sizeof(T)), full_bar);
+            mbar_arrive_expect_tx(full_bar, (uint32_t)((end - lo) * kMixBox * sizeof(T) + a.rec_bytes));
+            if (hi > lo)
+                tma_load_1d(smem_addr(ybuf + lo * kMixBox),
+                            static_cast<const T *>(a.src) + (int64_t)s * a.ld + (int64_t)(r0 + lo) * kMixBox,
+                            (uint32_t)((hi - lo) * kMixBox * sizeof(T)), full_bar);
             if (ragged)
-                tma_load_2d(smem_addr(ybuf + n_full * kMixBox), tmap, a.full_rows * kMixBox, s,
-                            full_bar);
+                tma_load_2d(smem_addr(ybuf + rr * kMixBox), tmap, a.full_rows * kMixBox, s, full_bar);
         }
-    } else {
-        if (lane == 0)
-            mbar_arrive_expect_tx(full_bar, (uint32_t)(a.buf_elems * sizeof(T) + a.rec_bytes));
-        __syncwarp();
-        for (int b = lane; b < n_box; b += 32)
-            tma_load_2d(smem_addr(ybuf + b * kMixBox), tmap, x0 + b * kMixBox, s, full_bar);
     }
     if (lane == 0)
         tma_load_1d(smem_addr(rbuf), a.table + (size_t)d * a.rec_bytes, (uint32_t)a.rec_bytes,
