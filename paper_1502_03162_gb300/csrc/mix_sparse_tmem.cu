@@ -254,13 +254,16 @@ __device__ __forceinline__ void issue_unit(const CUtensorMap *tmap, const CUtens
 {
     const int x0 = t * kTile - a.halo;
     const int n_box = a.buf_elems / kMixBox;
-    // The tile starts on a row of the 3-D view (x0 % kMixBox == 0).  An interior tile (every
-    // row it covers a full row of the source) is one 3-D request.  A tile at either end of the
-    // source: one bulk copy of the full rows it covers, one 2-D box for the ragged last row (zero
-    // fill past len), and 16-byte zero stores here for the rows before 0 or past the source,
-    // made before the arrive that publishes them.
+    // The tile starts on a row of the 3-D view (x0 % kMixBox == 0), whose rows are the full
+    // 256-sample rows of the source.  A window that does not contain the source's ragged last
+    // row is one 3-D request (rows before 0 or past the last full row arrive as hardware zero
+    // fill).  A window containing the ragged row (at most one per source): one bulk copy of the
+    // full rows it covers, one 2-D box for the ragged row (zero fill past len), and 16-byte
+    // zero stores here for the other rows, made before the arrive that publishes them.
     const int r0 = x0 >= 0 ? x0 / kMixBox : -((-x0 + kMixBox - 1) / kMixBox);
-    if (r0 >= 0 && r0 + n_box <= a.full_rows) {
+    const int rr = a.full_rows - r0;                                      // the ragged row, if any
+    const bool ragged_in = (int64_t)a.full_rows * kMixBox < a.len && rr >= 0 && rr < n_box;
+    if (a.full_rows > 0 && !ragged_in) {
         if (lane == 0) {
             mbar_arrive_expect_tx(full_bar, (uint32_t)(a.buf_elems * sizeof(T) + a.rec_bytes));
             tma_load_3d(smem_addr(ybuf), tmap3, 0, r0, s, full_bar);
@@ -269,8 +272,7 @@ __device__ __forceinline__ void issue_unit(const CUtensorMap *tmap, const CUtens
         const int lo = r0 < 0 ? (-r0 < n_box ? -r0 : n_box) : 0;         // rows before sample 0
         int hi = a.full_rows - r0;                                        // end of the full rows
         hi = hi < lo ? lo : (hi > n_box ? n_box : hi);
-        const int rr = a.full_rows - r0;                                  // the ragged row, if any
-        const bool ragged = (int64_t)a.full_rows * kMixBox < a.len && rr >= lo && rr < n_box;
+        const bool ragged = ragged_in && rr >= lo;
         const int end = ragged ? rr + 1 : hi;                             // rows [lo, end) hold data
         {
             const int per_row = kMixBox * (int)sizeof(T) / 16;
