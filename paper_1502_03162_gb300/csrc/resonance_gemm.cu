@@ -19,8 +19,8 @@
 // source window [t0 - 32, t0 + 4128) with 2-D tensor TMA (zero fill outside [0, len)); all
 // threads build A in the canonical no-swizzle K-major layout (8-row x 16-byte core
 // matrices); one thread issues the 12 MMAs (K = 16 each) and commits to an mbarrier; the 4
-// warps read the accumulator rows (tcgen05.ld, one TMEM lane per output block) and store u.
-// Waits are bounded.
+// warps read the accumulator rows (tcgen05.ld, one TMEM lane per output block) and store u
+// through shared memory as coalesced warp stores.  Waits are bounded.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -202,23 +202,39 @@ __global__ void __launch_bounds__(kThreads) resonance_gemm_kernel(const __grid_c
         ok = mbar_wait_bounded(smem_addr(&bars[1]), phase, abort_flag, a.status);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         phase ^= 1;
-        // ---- epilogue: TMEM lane = output block, 32 columns per ear ----
+        // ---- epilogue: TMEM lane = output block, 32 columns per ear.  A warp's 32 blocks
+        // are 1024 consecutive outputs, so each ear goes through the (now free) A tile in shared
+        // memory -- row = block, 16-byte chunk j of row L stored at chunk j ^ (L & 7), so that
+        // both the row writes and the contiguous reads are conflict-free -- and leaves as
+        // 512-byte coalesced warp stores. ----
         if (ok) {
-            const int row = warp * 32 + lane;
-            const int64_t n0 = t0 + (int64_t)row * kBlk;
-#pragma unroll
+            float *stg = reinterpret_cast<float *>(Am) + warp * 32 * kBlk;   // 4 KB per warp
+            const int64_t n_w = t0 + (int64_t)warp * 32 * kBlk;             // warp's first output
+#pragma unroll 1
             for (int e = 0; e < 2; ++e) {
                 float v[32];
                 tm_ld32(tmem + ((uint32_t)(warp * 32) << 16) + e * kBlk, v);
-                float *o = a.out + ((int64_t)s * 2 + e) * a.out_ld + n0;
-                if (n0 + kBlk <= a.out_len && ((uintptr_t)o & 15) == 0) {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        reinterpret_cast<float4 *>(o)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                } else {
-                    for (int i = 0; i < kBlk; ++i)
-                        if (n0 + i < a.out_len) o[i] = v[i];
+                for (int j = 0; j < 8; ++j)
+                    reinterpret_cast<float4 *>(stg + lane * kBlk)[j ^ (lane & 7)] =
+                        make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                __syncwarp();
+                float *o = a.out + ((int64_t)s * 2 + e) * a.out_ld + n_w;
+#pragma unroll
+                for (int it = 0; it < 8; ++it) {
+                    const int q = it * 32 + lane;                 // float4 chunk of the 1024
+                    const int row = q >> 3, j = q & 7;
+                    const float4 x = reinterpret_cast<const float4 *>(stg + row * kBlk)[j ^ (row & 7)];
+                    const int64_t n = n_w + 4 * q;
+                    if (n + 4 <= a.out_len) {
+                        *reinterpret_cast<float4 *>(o + 4 * q) = x;
+                    } else {
+                        if (n < a.out_len) o[4 * q] = x.x;
+                        if (n + 1 < a.out_len) o[4 * q + 1] = x.y;
+                        if (n + 2 < a.out_len) o[4 * q + 2] = x.z;
+                    }
                 }
+                __syncwarp();
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -1,6 +1,7 @@
 // tables.cu -- filter-pack kernels (sm_103a): top-K tap selection, the sparse tap records
 // consumed by the mixing kernel, and the dense HRIRs x = f * g (Eq. 1) for the baselines.
 #include <climits>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -31,34 +32,40 @@ __global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, 
         const int gi = j0 + j;
         v[j] = (j < per && gi < refl_len) ? gr[gi] : 0.0f;  // 0 is never selected
     }
-    uint64_t taken = 0;
-    int cnt = 0;
-    for (; cnt < k; ++cnt) {
-        float bv = 0.f;
-        int bi = INT_MAX;
+    // Each lane keeps its best remaining candidate as a key: the bits of a strictly positive
+    // float order like the float, 0 = none; on equal keys the smaller position (strict >).  A
+    // pick is the warp maximum of the keys, then the smallest index among the lanes holding
+    // it; only the winning lane rescans its slice.
+    using Mask = typename std::conditional<(MAXPER <= 32), uint32_t, uint64_t>::type;
+    Mask taken = 0;
+    uint32_t key = 0;
+    int pos = 0;
+    auto rescan = [&]() {
+        key = 0;
+        pos = 0;
 #pragma unroll
         for (int j = 0; j < MAXPER; ++j) {
-            const bool ok = !((taken >> j) & 1ull) && (v[j] > 0.f);
-            if (ok && (bi == INT_MAX || v[j] > bv)) {
-                bv = v[j];
-                bi = j0 + j;
+            const uint32_t b = __float_as_uint(v[j]);
+            if (!((taken >> j) & 1) && v[j] > 0.f && b > key) {
+                key = b;
+                pos = j;
             }
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-            const bool better = (oi != INT_MAX) && (bi == INT_MAX || ov > bv || (ov == bv && oi < bi));
-            if (better) {
-                bv = ov;
-                bi = oi;
-            }
+    };
+    rescan();
+    int cnt = 0;
+    for (; cnt < k; ++cnt) {
+        const uint32_t m = __reduce_max_sync(0xffffffffu, key);
+        if (m == 0) break;
+        const uint32_t cand = key == m ? (uint32_t)(j0 + pos) : 0xffffffffu;
+        const uint32_t win = __reduce_min_sync(0xffffffffu, cand);
+        if (cand == win) {
+            taken |= (Mask)1 << pos;
+            rescan();
         }
-        if (bi == INT_MAX) break;
-        if (bi >= j0 && bi < j0 + per) taken |= 1ull << (bi - j0);
     }
     // ascending-index output: lanes hold ascending slices; prefix-count the kept entries
-    const int mine = __popcll(taken);
+    const int mine = MAXPER <= 32 ? __popc((uint32_t)taken) : __popcll((uint64_t)taken);
     int before = mine;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -71,7 +78,7 @@ __global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, 
     int o = before;
 #pragma unroll
     for (int j = 0; j < MAXPER; ++j) {
-        if ((taken >> j) & 1ull) {
+        if ((taken >> j) & 1) {
             ri[o] = (uint16_t)(j0 + j);
             rw[o] = v[j];
             ++o;
