@@ -11,8 +11,9 @@
 // window segment of SW = 204 filter offsets, row (lane) holds the 256 samples
 // y[n - (seg+1) SW .. n - (seg+1) SW + 256) of its outputs' window.  A tap at offset o then
 // needs y[n + r - o] for r < R, the contiguous column range starting at (seg+1) SW - o: one
-// warp-uniform tcgen05.ld of 52 columns (no branch, no register indexing) followed by 52
-// FMAs; the next tap's load is in flight while the current tap's FMAs issue.
+// warp-uniform tcgen05.ld of 52 columns (no branch, no register indexing) followed by 26
+// packed FP32 FMAs (fma.rn.f32x2, two outputs each); the next tap's load is in flight while
+// the current tap's FMAs issue.
 //
 // The window is double-buffered in the 512 TMEM columns: while a pair of warps applies its
 // taps to one buffer, each warp copies half of the next window (shared memory -> registers
@@ -148,11 +149,17 @@ __device__ __forceinline__ void tm_ld(uint32_t taddr, uint32_t (&v)[R])
                  : "memory");
 }
 
+// Accumulators: the R outputs of a lane as R/2 pairs, each a 64-bit register pair that one
+// packed FP32 FMA (fma.rn.f32x2: two independent round-to-nearest FMAs, the same results as
+// two fmaf) updates, so a tap costs R/2 FMA instructions.
+constexpr int RP = R / 2;
+static_assert(R % 2 == 0, "outputs per lane in pairs");
+
 // Wait for this thread's outstanding tcgen05.ld.  v and acc are threaded through the
 // statements (volatile statements keep their order), so no use of the loaded registers moves
 // above the wait and every FMA into acc issued before it stays before it: the FMAs of
 // consecutive taps are never interleaved on the same accumulator.
-__device__ __forceinline__ void tm_wait_ld(uint32_t (&v)[R], float (&acc)[R])
+__device__ __forceinline__ void tm_wait_ld(uint32_t (&v)[R], uint64_t (&acc)[RP])
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25])
@@ -163,33 +170,32 @@ __device__ __forceinline__ void tm_wait_ld(uint32_t (&v)[R], float (&acc)[R])
                  :
                  : "memory");
     asm volatile(""
-                 : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]), "+f"(acc[6]), "+f"(acc[7]), "+f"(acc[8]), "+f"(acc[9]), "+f"(acc[10]), "+f"(acc[11]), "+f"(acc[12]), "+f"(acc[13]), "+f"(acc[14]), "+f"(acc[15]), "+f"(acc[16]), "+f"(acc[17]), "+f"(acc[18]), "+f"(acc[19]), "+f"(acc[20]), "+f"(acc[21]), "+f"(acc[22]), "+f"(acc[23]), "+f"(acc[24]), "+f"(acc[25])
-                 :
-                 : "memory");
-    asm volatile(""
-                 : "+f"(acc[26]), "+f"(acc[27]), "+f"(acc[28]), "+f"(acc[29]), "+f"(acc[30]), "+f"(acc[31]), "+f"(acc[32]), "+f"(acc[33]), "+f"(acc[34]), "+f"(acc[35]), "+f"(acc[36]), "+f"(acc[37]), "+f"(acc[38]), "+f"(acc[39]), "+f"(acc[40]), "+f"(acc[41]), "+f"(acc[42]), "+f"(acc[43]), "+f"(acc[44]), "+f"(acc[45]), "+f"(acc[46]), "+f"(acc[47]), "+f"(acc[48]), "+f"(acc[49]), "+f"(acc[50]), "+f"(acc[51])
+                 : "+l"(acc[0]), "+l"(acc[1]), "+l"(acc[2]), "+l"(acc[3]), "+l"(acc[4]), "+l"(acc[5]), "+l"(acc[6]), "+l"(acc[7]), "+l"(acc[8]), "+l"(acc[9]), "+l"(acc[10]), "+l"(acc[11]), "+l"(acc[12]), "+l"(acc[13]), "+l"(acc[14]), "+l"(acc[15]), "+l"(acc[16]), "+l"(acc[17]), "+l"(acc[18]), "+l"(acc[19]), "+l"(acc[20]), "+l"(acc[21]), "+l"(acc[22]), "+l"(acc[23]), "+l"(acc[24]), "+l"(acc[25])
                  :
                  : "memory");
 }
 
 // Keep every FMA into acc after this point (issued after a TMEM load, so that the load is
 // in flight while they run).
-__device__ __forceinline__ void tie_acc(float (&acc)[R])
+__device__ __forceinline__ void tie_acc(uint64_t (&acc)[RP])
 {
     asm volatile(""
-                 : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]), "+f"(acc[6]), "+f"(acc[7]), "+f"(acc[8]), "+f"(acc[9]), "+f"(acc[10]), "+f"(acc[11]), "+f"(acc[12]), "+f"(acc[13]), "+f"(acc[14]), "+f"(acc[15]), "+f"(acc[16]), "+f"(acc[17]), "+f"(acc[18]), "+f"(acc[19]), "+f"(acc[20]), "+f"(acc[21]), "+f"(acc[22]), "+f"(acc[23]), "+f"(acc[24]), "+f"(acc[25])
-                 :
-                 : "memory");
-    asm volatile(""
-                 : "+f"(acc[26]), "+f"(acc[27]), "+f"(acc[28]), "+f"(acc[29]), "+f"(acc[30]), "+f"(acc[31]), "+f"(acc[32]), "+f"(acc[33]), "+f"(acc[34]), "+f"(acc[35]), "+f"(acc[36]), "+f"(acc[37]), "+f"(acc[38]), "+f"(acc[39]), "+f"(acc[40]), "+f"(acc[41]), "+f"(acc[42]), "+f"(acc[43]), "+f"(acc[44]), "+f"(acc[45]), "+f"(acc[46]), "+f"(acc[47]), "+f"(acc[48]), "+f"(acc[49]), "+f"(acc[50]), "+f"(acc[51])
+                 : "+l"(acc[0]), "+l"(acc[1]), "+l"(acc[2]), "+l"(acc[3]), "+l"(acc[4]), "+l"(acc[5]), "+l"(acc[6]), "+l"(acc[7]), "+l"(acc[8]), "+l"(acc[9]), "+l"(acc[10]), "+l"(acc[11]), "+l"(acc[12]), "+l"(acc[13]), "+l"(acc[14]), "+l"(acc[15]), "+l"(acc[16]), "+l"(acc[17]), "+l"(acc[18]), "+l"(acc[19]), "+l"(acc[20]), "+l"(acc[21]), "+l"(acc[22]), "+l"(acc[23]), "+l"(acc[24]), "+l"(acc[25])
                  :
                  : "memory");
 }
 
-__device__ __forceinline__ void fma_slice(float (&acc)[R], const uint32_t (&v)[R], float w)
+// acc[i] += w * (v[2i], v[2i+1]) for the R outputs of the lane
+__device__ __forceinline__ void fma_slice(uint64_t (&acc)[RP], const uint32_t (&v)[R], uint32_t w)
 {
+    uint64_t ww;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(ww) : "r"(w));
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = fmaf(w, __uint_as_float(v[r]), acc[r]);
+    for (int i = 0; i < RP; ++i) {
+        uint64_t x;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "r"(v[2 * i]), "r"(v[2 * i + 1]));
+        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[i]) : "l"(ww), "l"(x));
+    }
 }
 
 // Barrier of the two warps of lane quarter q (named barrier 1 + q, 64 threads) that also
@@ -225,7 +231,7 @@ __device__ __forceinline__ void copy_half(const T *src, uint32_t dst)
 // Apply n taps {column, weight bits} of this warp's ear to acc (n even: the lists are padded
 // with zero-weight taps, and at least 4 readable entries follow each list).  TMEM loads are
 // double-buffered: the next tap's slice is in flight while the current tap's FMAs issue.
-__device__ __forceinline__ void apply_taps(float (&acc)[R], uint32_t tw, const int2 *taps, int n)
+__device__ __forceinline__ void apply_taps(uint64_t (&acc)[RP], uint32_t tw, const int2 *taps, int n)
 {
     if (n <= 0) return;
     uint32_t A[R], B[R];
@@ -236,11 +242,11 @@ __device__ __forceinline__ void apply_taps(float (&acc)[R], uint32_t tw, const i
         tm_wait_ld(A, acc);
         tm_ld(tw + (uint32_t)t1.x, B);
         tie_acc(acc);
-        fma_slice(acc, A, __int_as_float(t0.y));
+        fma_slice(acc, A, (uint32_t)t0.y);
         tm_wait_ld(B, acc);
         if (i + 2 < n) tm_ld(tw + (uint32_t)t2.x, A);
         tie_acc(acc);
-        fma_slice(acc, B, __int_as_float(t1.y));
+        fma_slice(acc, B, (uint32_t)t1.y);
         t0 = t2;
         t1 = t3;
     }
@@ -421,9 +427,9 @@ __global__ void __launch_bounds__(NW * 32, 1)
         const int lane_off = (q * 32 + lane) * R;
         const int n_seg = a.nseg;
         const int64_t n_steps = (int64_t)n_units * n_seg;
-        float acc[R];
+        uint64_t acc[RP];
 #pragma unroll
-        for (int i = 0; i < R; ++i) acc[i] = 0.f;
+        for (int i = 0; i < RP; ++i) acc[i] = 0;
         int slot = a.part.slot_base(blockIdx.x, pos0.t), run_n = 0;
 
         // the window of a step (stage st, segment seg) for this warp's half
@@ -488,10 +494,14 @@ __global__ void __launch_bounds__(NW * 32, 1)
                     float4 *p = reinterpret_cast<float4 *>(
                         a.partial + ((size_t)pos.t * a.slots + slot) * 2 * kTile + ear * kTile + lane_off);
 #pragma unroll
-                    for (int i = 0; i < R / 4; ++i)
-                        p[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+                    for (int i = 0; i < R / 4; ++i) {
+                        float x0, x1, x2, x3;
+                        asm("mov.b64 {%0, %1}, %2;" : "=f"(x0), "=f"(x1) : "l"(acc[2 * i]));
+                        asm("mov.b64 {%0, %1}, %2;" : "=f"(x2), "=f"(x3) : "l"(acc[2 * i + 1]));
+                        p[i] = make_float4(x0, x1, x2, x3);
+                    }
 #pragma unroll
-                    for (int i = 0; i < R; ++i) acc[i] = 0.f;
+                    for (int i = 0; i < RP; ++i) acc[i] = 0;
                     ++slot;
                     run_n = 0;
                 }
