@@ -112,8 +112,8 @@ int hrir_topk_pack(hrir_ctx *ctx, int n_rows, int refl_len, int k, const float *
  *   tap_w      float  [n_dirs][2][k_max]: finite and >= 0 (g >= 0, Eq. 1).
  *   tap_nnz    uint8  [n_dirs][2]: used slots, <= k_max.
  *   res_len    Lf, 1 .. 512;  resonance float [2][res_len], finite.
- *   fft_size   overlap-save frame P for HRIR_FFT (power of two, 512..8192, > H),
- *              or 0 to choose automatically.
+ *   fft_size   overlap-save frame P for HRIR_FFT: 0 or 4096 (the frame the FFT kernels
+ *              implement; H - 1 rounded up to 8 must be < P), anything else is HRIR_EINVAL.
  * ------------------------------------------------------------------------------------- */
 int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k_max,
                       const uint16_t *tap_idx, const float *tap_w, const uint8_t *tap_nnz,

@@ -366,7 +366,7 @@ int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k
         return fail(ctx, HRIR_EINVAL, "NULL table pointer");
     const int hrir_len = res_len + refl_len - 1;
     if (fft_size != 0 && fft_size != kFftSize)
-        return fail(ctx, HRIR_EINVAL, "fft_size %d: this build implements P = %d (pass 0 or %d)",
+        return fail(ctx, HRIR_EINVAL, "fft_size %d: the FFT path implements P = %d (pass 0 or %d)",
                     fft_size, kFftSize, kFftSize);
     if ((int)round_up(hrir_len - 1, 8) >= kFftSize)
         return fail(ctx, HRIR_EINVAL, "HRIR length %d too long for the P = %d FFT frame", hrir_len, kFftSize);
