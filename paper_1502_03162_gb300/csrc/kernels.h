@@ -20,20 +20,22 @@ namespace hrir {
 #define HRIR_DENSE_WARPS 8
 #endif
 // Sparse kernel: windows in tensor memory.  4 TMEM lane quarters x 32 lanes x R = 52
-// consecutive outputs per lane (tile 6656); the two warps of a lane quarter (one per ear)
-// share a window of kSparseTmemCols samples = one segment of kSparseSegment filter offsets
-// plus the lane's outputs, double-buffered in the 512 TMEM columns; one more warp issues the
-// TMA loads.
-constexpr int kSparseR = 52, kSparseWarps = 8, kSparseQuarters = 4;
+// consecutive outputs per lane (tile 6656); the two tap warps of a lane quarter (one per ear)
+// read a window of kSparseTmemCols samples = one segment of kSparseSegment filter offsets
+// plus the lane's outputs, which the quarter's copy warp writes, double-buffered in the 512
+// TMEM columns (16 tap warps + 4 copy warps + 1 warp that issues the TMA loads).
+constexpr int kSparseR = 52, kSparseWarps = 21, kSparseQuarters = 4;
 constexpr int kSparseTile = kSparseQuarters * 32 * kSparseR;
 constexpr int kSparseTmemCols = 256;
 constexpr int kSparseSegment = kSparseTmemCols - kSparseR;  // 204
 constexpr int kDenseR = HRIR_DENSE_R, kDenseWarps = HRIR_DENSE_WARPS;
 constexpr int kMixMaxStages = 6;
 constexpr int kMixDirCache = 2048;                // unit directions staged in shared memory
-// shared memory after the stage ring and its barriers: abort flag + TMEM slot (16 B), the
-// per-stage release counters and last issued units, the direction cache
-constexpr int kMixSmemTail = 16 + 2 * kMixMaxStages * 4 + kMixDirCache * 4;
+// shared memory after the stage ring and its barriers: 16 window barriers (sparse kernel),
+// abort flag + TMEM slot (16 B), the per-stage release counters and last issued units, the
+// direction cache
+constexpr int kMixWindowBars = 16;
+constexpr int kMixSmemTail = kMixWindowBars * 8 + 16 + 2 * kMixMaxStages * 4 + kMixDirCache * 4;
 constexpr int kMixBox = 256;                      // TMA box width (elements)
 constexpr int kRunSources = 64;                   // max sources per register accumulation run
 
@@ -200,6 +202,7 @@ struct MovingArgs {
     int refl_len;
     int halo;                    // round_up(refl_len, 4)
     int n_js;                    // segments staged per unit
+    int bulk_tables;             // tables copied by bulk copies (k_max % 4 == 0, 16-byte aligned)
     Partition part;
     float *partial;              // [n_tiles][slots][2][kMovTile]
     int slots;
@@ -207,6 +210,7 @@ struct MovingArgs {
 };
 size_t moving_smem_bytes(int halo, int n_js, int k_max);
 cudaError_t launch_moving_mix(const MovingArgs &a, int grid, size_t smem, cudaStream_t st);
+int moving_ctas_per_sm(size_t smem);   // resident CTAs per SM (>= 1)
 
 // ---- per-source resonance as a Toeplitz-block GEMM on the tensor cores ----------------------
 constexpr int kResTile = 4096;   // outputs per MMA tile (128 blocks of 32)
@@ -222,6 +226,7 @@ struct ResonanceArgs {
 };
 size_t resonance_gemm_smem_bytes(int elem_bytes);
 // tmap: 2-D tensor map over the 16-bit sources with box {256, 1}
+int resonance_gemm_ctas_per_sm(int dtype);   // resident CTAs per SM (>= 1)
 cudaError_t launch_resonance_gemm(int dtype, const CUtensorMap &tmap, const ResonanceArgs &a,
                                   int grid, cudaStream_t st);
 

@@ -301,9 +301,16 @@ int hrir_render_moving(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, co
         return fail(ctx, HRIR_EINVAL, "src must be 16-byte aligned with src_ld >= len, src_ld %% 4 == 0");
     const int64_t mix_len = std::min<int64_t>(out_len, len + ctx->refl_len - 1);
     const int n_tiles = (int)((mix_len + kMovTile - 1) / kMovTile);
+    const int halo = (int)round_up(ctx->refl_len, 4);
+    const int n_js = (kMovTile + seg_len - 1) / seg_len + 2;
+    if (halo > kMovMaxHalo || (int64_t)n_js * 2 * k_max > kMovMaxTaps || n_js * 2 > 32)
+        return fail(ctx, HRIR_EINVAL, "reflection filters too long (Lg <= %d) or too many taps for "
+                    "the segment length (%d segments x 2 ears x k_max <= %d)", kMovMaxHalo, n_js, kMovMaxTaps);
+    const size_t smem = moving_smem_bytes(halo, n_js, k_max);
+    // one resident wave of persistent CTAs (each takes an equal share of the units)
     Partition part;
     part.U = (int64_t)n_tiles * n_src;
-    part.P = std::min<int64_t>((int64_t)ctx->num_sms * 4, part.U);
+    part.P = std::min<int64_t>((int64_t)ctx->num_sms * moving_ctas_per_sm(smem), part.U);
     part.n_src = n_src;
     part.gs = kRunSources;
     int slots = 0;
@@ -323,16 +330,13 @@ int hrir_render_moving(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, co
     a.tap_w = tap_w;
     a.tap_nnz = tap_nnz;
     a.refl_len = ctx->refl_len;
-    a.halo = (int)round_up(ctx->refl_len, 4);
-    a.n_js = (kMovTile + seg_len - 1) / seg_len + 2;
+    a.halo = halo;
+    a.n_js = n_js;
+    a.bulk_tables = (k_max % 4 == 0) && ((uintptr_t)tap_idx % 16 == 0) && ((uintptr_t)tap_w % 16 == 0);
     a.part = part;
     a.partial = ctx->d_partial;
     a.slots = slots;
     a.status = ctx->d_status;
-    const size_t smem = moving_smem_bytes(a.halo, a.n_js, k_max);
-    if (a.halo > kMovMaxHalo || (int64_t)a.n_js * 2 * k_max > kMovMaxTaps)
-        return fail(ctx, HRIR_EINVAL, "reflection filters too long (Lg <= %d) or too many taps for "
-                    "the segment length (%d segments x 2 ears x k_max <= %d)", kMovMaxHalo, a.n_js, kMovMaxTaps);
     {
         KernelTimer kt(ctx, HRIR_K_MOVING, st);
         HRIR_CUDA_TRY(ctx, launch_moving_mix(a, (int)part.P, smem, st));
@@ -389,7 +393,7 @@ int hrir_resonance_per_source(hrir_ctx *ctx, int n_src, int64_t len, int64_t src
     a.out_ld = out_ld;
     a.status = ctx->d_status;
     const int64_t units = ((out_len + kResTile - 1) / kResTile) * n_src;
-    const int grid = (int)std::min<int64_t>(units, (int64_t)ctx->num_sms * 4);
+    const int grid = (int)std::min<int64_t>(units, (int64_t)ctx->num_sms * resonance_gemm_ctas_per_sm((int)dt));
     KernelTimer kt(ctx, HRIR_K_RESONANCE, st);
     HRIR_CUDA_TRY(ctx, launch_resonance_gemm((int)dt, tmap, a, grid, st));
     kt.done();

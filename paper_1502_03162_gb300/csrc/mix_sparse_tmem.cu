@@ -6,26 +6,28 @@
 // with each lane's source window held in tensor memory (TMEM).
 //
 // A tile of 6656 outputs is split over the 4 TMEM lane quarters x 32 lanes, R = 52
-// consecutive outputs per lane.  The two warps of a lane quarter (warp q: left ear, warp
-// q + 4: right ear) share that quarter's TMEM rows.  For every (source, tile) unit and every
-// window segment of SW = 204 filter offsets, row (lane) holds the 256 samples
-// y[n - (seg+1) SW .. n - (seg+1) SW + 256) of its outputs' window.  A tap at offset o then
-// needs y[n + r - o] for r < R, the contiguous column range starting at (seg+1) SW - o: one
-// warp-uniform tcgen05.ld of 52 columns (no branch, no register indexing) followed by 26
-// packed FP32 FMAs (fma.rn.f32x2, two outputs each); the next tap's load is in flight while
-// the current tap's FMAs issue.
+// consecutive outputs per lane.  Five warps share each lane quarter q: four tap warps
+// q + 4 (ear + 2 half) read its TMEM rows, each for one ear and one half (26 outputs) of every
+// lane's outputs, and copy warp q + 16 writes them.  For every (source, tile) unit and every window segment of SW = 204 filter offsets,
+// row (lane) holds the 256 samples y[n - (seg+1) SW .. n - (seg+1) SW + 256) of its outputs'
+// window.  A tap at offset o then needs y[n + r - o] for r < R, the contiguous column range
+// starting at (seg+1) SW - o, of which a tap warp reads its half: one warp-uniform
+// tcgen05.ld of 26 columns (no branch, no register indexing) followed by 13 packed FP32 FMAs
+// (fma.rn.f32x2, two outputs each).
 //
-// The window is double-buffered in the 512 TMEM columns: while a pair of warps applies its
-// taps to one buffer, each warp copies half of the next window (shared memory -> registers
-// -> tcgen05.st) into the other, the left-ear warp before its taps and the right-ear warp
-// after them; a named barrier per pair (with
-// an AND vote, so that both warps leave together on a timeout) hands the buffers over.
+// The window is double-buffered in the 512 TMEM columns.  The copy warp of a quarter fills
+// one buffer (shared memory -> registers -> tcgen05.st) while the quarter's tap warps apply
+// their taps to the other, so the shared-memory-bound copy and the FMA-bound taps run at the
+// same time on different warps; per quarter and buffer a "full" mbarrier (copy warp -> tap
+// warps) and an "empty" mbarrier (tap warps -> copy warp) hand the buffers over.
 // A ring of up to 6 shared-memory stages holds each unit's source tile (tensor TMA, 256-sample
-// halo, hardware zero fill outside [0, len)) and the direction's tap record (bulk copy): the
-// last of the 8 warps to release a stage refills it at once with the unit `stages` ahead.
+// halo, hardware zero fill outside [0, len)) and the direction's tap record (bulk copy); a
+// producer warp issues every load, refilling each stage with the unit `stages` ahead as soon
+// as the 20 compute warps have released it.
 // Work is a persistent balanced range of units per CTA; register accumulators are
 // flushed every <= 64 sources into partial slots that the reduction sums in a fixed order.
-// All waits are bounded.
+// All waits are bounded: a wait that expires raises the CTA's abort flag, and every other
+// wait then returns at once, so all warps leave their loops.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -37,16 +39,21 @@ namespace {
 
 constexpr int R = kSparseR;             // outputs per lane
 constexpr int NQ = kSparseQuarters;     // TMEM lane quarters
-constexpr int NW = kSparseWarps;        // warps: (lane quarter, ear); warp 0 also issues TMA
+constexpr int NH = 2;                   // tap warps per (lane quarter, ear), R / NH outputs each
+constexpr int RS = R / NH;              // outputs of a lane per tap warp
+constexpr int NTW = 2 * NH * NQ;        // tap warps (lane quarter, ear, half)
+constexpr int NC = NTW + NQ;            // compute warps: tap warps + one copy warp per quarter
+constexpr int NW = kSparseWarps;        // compute warps + the producer warp (TMA issue)
 constexpr int kTile = kSparseTile;      // outputs per tile
 constexpr int kCols = kSparseTmemCols;  // TMEM columns per window buffer
 constexpr int SW = kSparseSegment;      // filter offsets per window segment (= kCols - R)
-constexpr int kHalf = kCols / 2;        // window columns each warp of a pair copies
-constexpr int kCopyChunks = kHalf / 32; // tcgen05.st.x32 per warp per window
-static_assert(NW == 2 * NQ, "one warp per (lane quarter, ear)");
+constexpr int kCopyChunks = 1;          // tcgen05.st.x32 per copy batch (32 columns)
+static_assert(NW == NC + 1 && NTW % NQ == 0, "compute warp w works on TMEM lane quarter w % 4");
+static_assert(kCols % (32 * kCopyChunks) == 0, "a window is whole copy batches");
+static_assert(kMixWindowBars == 4 * NQ, "a full and an empty barrier per quarter and buffer");
 static_assert(SW + R == kCols && 2 * kCols == 512, "two window buffers fill the 512 columns");
 static_assert(R % 4 == 0 && ((R / 4) & 1), "lane stride must be an odd number of 16-byte groups");
-static_assert(R == 32 + 16 + 4, "a slice is loaded as x32 + x16 + x4 columns");
+static_assert(RS == 16 + 8 + 2, "a slice is loaded as x16 + x8 + x2 columns");
 static_assert(kTile % kMixBox == 0, "tiles start on a row of the 3-D source view");
 
 // ---- 32 consecutive samples, widened to FP32 (conflict-free: the lane stride R is an odd
@@ -121,56 +128,41 @@ __device__ __forceinline__ void tm_st32(uint32_t taddr, const uint32_t (&v)[32])
 
 __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// R = 52 columns starting at taddr into v (async; valid after tm_wait_ld(v))
-__device__ __forceinline__ void tm_ld(uint32_t taddr, uint32_t (&v)[R])
+// RS = 26 columns starting at taddr into v (async; valid after tm_wait_ld(v))
+__device__ __forceinline__ void tm_ld(uint32_t taddr, uint32_t (&v)[RS])
 {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-        "%30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr)
-        : "memory");
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-        "%12, %13, %14, %15}, [%16];"
-        : "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]),
-          "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]),
-          "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47])
-        : "r"(taddr + 32)
-        : "memory");
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51])
-                 : "r"(taddr + 48)
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23])
+                 : "r"(taddr + 16)
+                 : "memory");
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                 : "=r"(v[24]), "=r"(v[25])
+                 : "r"(taddr + 24)
                  : "memory");
 }
 
-// Accumulators: the R outputs of a lane as R/2 pairs, each a 64-bit register pair that one
+// Accumulators: the RS outputs of a lane as RS/2 pairs, each a 64-bit register pair that one
 // packed FP32 FMA (fma.rn.f32x2: two independent round-to-nearest FMAs, the same results as
-// two fmaf) updates, so a tap costs R/2 FMA instructions.
-constexpr int RP = R / 2;
-static_assert(R % 2 == 0, "outputs per lane in pairs");
+// two fmaf) updates, so a tap costs RS/2 FMA instructions.
+constexpr int RP = RS / 2;
+static_assert(RS % 2 == 0, "outputs per lane in pairs");
 
 // Wait for this thread's outstanding tcgen05.ld.  v and acc are threaded through the
 // statements (volatile statements keep their order), so no use of the loaded registers moves
 // above the wait and every FMA into acc issued before it stays before it: the FMAs of
 // consecutive taps are never interleaved on the same accumulator.
-__device__ __forceinline__ void tm_wait_ld(uint32_t (&v)[R], uint64_t (&acc)[RP])
+__device__ __forceinline__ void tm_wait_ld(uint32_t (&v)[RS], uint64_t (&acc)[RP])
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25])
                  :
                  : "memory");
     asm volatile(""
-                 : "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31]), "+r"(v[32]), "+r"(v[33]), "+r"(v[34]), "+r"(v[35]), "+r"(v[36]), "+r"(v[37]), "+r"(v[38]), "+r"(v[39]), "+r"(v[40]), "+r"(v[41]), "+r"(v[42]), "+r"(v[43]), "+r"(v[44]), "+r"(v[45]), "+r"(v[46]), "+r"(v[47]), "+r"(v[48]), "+r"(v[49]), "+r"(v[50]), "+r"(v[51])
-                 :
-                 : "memory");
-    asm volatile(""
-                 : "+l"(acc[0]), "+l"(acc[1]), "+l"(acc[2]), "+l"(acc[3]), "+l"(acc[4]), "+l"(acc[5]), "+l"(acc[6]), "+l"(acc[7]), "+l"(acc[8]), "+l"(acc[9]), "+l"(acc[10]), "+l"(acc[11]), "+l"(acc[12]), "+l"(acc[13]), "+l"(acc[14]), "+l"(acc[15]), "+l"(acc[16]), "+l"(acc[17]), "+l"(acc[18]), "+l"(acc[19]), "+l"(acc[20]), "+l"(acc[21]), "+l"(acc[22]), "+l"(acc[23]), "+l"(acc[24]), "+l"(acc[25])
+                 : "+l"(acc[0]), "+l"(acc[1]), "+l"(acc[2]), "+l"(acc[3]), "+l"(acc[4]), "+l"(acc[5]), "+l"(acc[6]), "+l"(acc[7]), "+l"(acc[8]), "+l"(acc[9]), "+l"(acc[10]), "+l"(acc[11]), "+l"(acc[12])
                  :
                  : "memory");
 }
@@ -180,13 +172,13 @@ __device__ __forceinline__ void tm_wait_ld(uint32_t (&v)[R], uint64_t (&acc)[RP]
 __device__ __forceinline__ void tie_acc(uint64_t (&acc)[RP])
 {
     asm volatile(""
-                 : "+l"(acc[0]), "+l"(acc[1]), "+l"(acc[2]), "+l"(acc[3]), "+l"(acc[4]), "+l"(acc[5]), "+l"(acc[6]), "+l"(acc[7]), "+l"(acc[8]), "+l"(acc[9]), "+l"(acc[10]), "+l"(acc[11]), "+l"(acc[12]), "+l"(acc[13]), "+l"(acc[14]), "+l"(acc[15]), "+l"(acc[16]), "+l"(acc[17]), "+l"(acc[18]), "+l"(acc[19]), "+l"(acc[20]), "+l"(acc[21]), "+l"(acc[22]), "+l"(acc[23]), "+l"(acc[24]), "+l"(acc[25])
+                 : "+l"(acc[0]), "+l"(acc[1]), "+l"(acc[2]), "+l"(acc[3]), "+l"(acc[4]), "+l"(acc[5]), "+l"(acc[6]), "+l"(acc[7]), "+l"(acc[8]), "+l"(acc[9]), "+l"(acc[10]), "+l"(acc[11]), "+l"(acc[12])
                  :
                  : "memory");
 }
 
-// acc[i] += w * (v[2i], v[2i+1]) for the R outputs of the lane
-__device__ __forceinline__ void fma_slice(uint64_t (&acc)[RP], const uint32_t (&v)[R], uint32_t w)
+// acc[i] += w * (v[2i], v[2i+1]) for the RS outputs of the lane
+__device__ __forceinline__ void fma_slice(uint64_t (&acc)[RP], const uint32_t (&v)[RS], uint32_t w)
 {
     uint64_t ww;
     asm("mov.b64 %0, {%1, %1};" : "=l"(ww) : "r"(w));
@@ -198,57 +190,41 @@ __device__ __forceinline__ void fma_slice(uint64_t (&acc)[RP], const uint32_t (&
     }
 }
 
-// Barrier of the two warps of lane quarter q (named barrier 1 + q, 64 threads) that also
-// returns the AND of `ok` over them; TMEM accesses before it are ordered before those after.
-__device__ __forceinline__ bool pair_sync_all(int q, bool ok)
-{
-    uint32_t r;
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    asm volatile(
-        "{\n\t.reg .pred p, v;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.and.pred v, %2, 64, p;\n\t"
-        "selp.u32 %0, 1, 0, v;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)ok), "r"(1 + q)
-        : "memory");
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    return r != 0;
-}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// This warp's half of a window (kHalf columns of its 32 TMEM lanes): shared memory ->
-// registers -> tcgen05.st, all loads issued before the first store.
+// One window (kCols columns of this warp's 32 TMEM lanes): shared memory -> registers ->
+// tcgen05.st, in batches of kCopyChunks x 32 columns whose loads all issue before their
+// stores.
 template <typename T>
-__device__ __forceinline__ void copy_half(const T *src, uint32_t dst)
+__device__ __forceinline__ void copy_window(const T *src, uint32_t dst)
 {
-    uint32_t v[kCopyChunks][32];
+#pragma unroll 1
+    for (int b = 0; b < kCols; b += 32 * kCopyChunks) {
+        uint32_t v[kCopyChunks][32];
 #pragma unroll
-    for (int c = 0; c < kCopyChunks; ++c) Load32<T>::run(src + 32 * c, v[c]);
+        for (int c = 0; c < kCopyChunks; ++c) Load32<T>::run(src + b + 32 * c, v[c]);
 #pragma unroll
-    for (int c = 0; c < kCopyChunks; ++c) tm_st32(dst + 32 * c, v[c]);
+        for (int c = 0; c < kCopyChunks; ++c) tm_st32(dst + (uint32_t)(b + 32 * c), v[c]);
+    }
 }
 
-// Apply n taps {column, weight bits} of this warp's ear to acc (n even: the lists are padded
-// with zero-weight taps, and at least 4 readable entries follow each list).  TMEM loads are
-// double-buffered: the next tap's slice is in flight while the current tap's FMAs issue.
+// Apply n taps {column, weight bits} of this warp's ear to acc (at least 4 readable entries
+// follow each list).  One slice in registers at a time: the load latency of one tap warp is
+// covered by the FMAs of the other three tap warps on the same SM sub-partition; the next
+// tap's entry is read from shared memory while the current slice is in flight.
 __device__ __forceinline__ void apply_taps(uint64_t (&acc)[RP], uint32_t tw, const int2 *taps, int n)
 {
-    if (n <= 0) return;
-    uint32_t A[R], B[R];
-    int2 t0 = taps[0], t1 = taps[1];
-    tm_ld(tw + (uint32_t)t0.x, A);
-    for (int i = 0; i < n; i += 2) {
-        const int2 t2 = taps[i + 2], t3 = taps[i + 3];
+    uint32_t A[RS];
+    int2 t = taps[0];
+#pragma unroll 2
+    for (int i = 0; i < n; ++i) {
+        tm_ld(tw + (uint32_t)t.x, A);
+        const int2 tn = taps[i + 1];
         tm_wait_ld(A, acc);
-        tm_ld(tw + (uint32_t)t1.x, B);
-        tie_acc(acc);
-        fma_slice(acc, A, (uint32_t)t0.y);
-        tm_wait_ld(B, acc);
-        if (i + 2 < n) tm_ld(tw + (uint32_t)t2.x, A);
-        tie_acc(acc);
-        fma_slice(acc, B, (uint32_t)t1.y);
-        t0 = t2;
-        t1 = t3;
+        fma_slice(acc, A, (uint32_t)t.y);
+        tie_acc(acc);      // these FMAs read A before the next load overwrites it
+        t = tn;
     }
 }
 
@@ -331,7 +307,7 @@ __device__ __forceinline__ int checked_dir(const MixArgs &a, int d, int lane)
 // segment its left taps and right taps as int2 {window column, weight bits}, each list padded
 // to an even length with zero-weight taps, and 4 padding entries at the end.
 template <typename T>
-__global__ void __launch_bounds__(NW * 32, 1)
+__global__ void __maxnreg__(80)
     sparse_tmem_kernel(const __grid_constant__ CUtensorMap tmap,
                        const __grid_constant__ CUtensorMap tmap3, const MixArgs a)
 {
@@ -340,10 +316,10 @@ __global__ void __launch_bounds__(NW * 32, 1)
     T *ybuf = reinterpret_cast<T *>(smem);
     unsigned char *rbuf = smem + (size_t)stages * a.buf_elems * sizeof(T);
     uint64_t *bars = reinterpret_cast<uint64_t *>(rbuf + (size_t)stages * a.rec_bytes);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * stages);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages) + 1;
-    int *relcnt = reinterpret_cast<int *>(bars + 2 * stages) + 4;      // [kMixMaxStages]
-    int *last_issued = relcnt + kMixMaxStages;                         // [kMixMaxStages]
+    uint64_t *wbars = bars + 2 * stages;        // [full, empty][quarter][buffer]
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(wbars + kMixWindowBars);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wbars + kMixWindowBars) + 1;
+    int *last_issued = reinterpret_cast<int *>(wbars + kMixWindowBars) + 4;  // [kMixMaxStages]
     int *dircache = last_issued + kMixMaxStages;                       // [kMixDirCache]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -352,13 +328,14 @@ __global__ void __launch_bounds__(NW * 32, 1)
         prefetch_tensormap(&tmap3);
         for (int i = 0; i < stages; ++i) {
             mbar_init(smem_addr(&bars[i]), 1);              // full: producer + tx bytes
-            mbar_init(smem_addr(&bars[stages + i]), NW);    // empty: one arrive per warp
+            mbar_init(smem_addr(&bars[stages + i]), NC);    // empty: one arrive per compute warp
+        }
+        for (int i = 0; i < 2 * NQ; ++i) {
+            mbar_init(smem_addr(&wbars[i]), 1);             // window full: the copy warp
+            mbar_init(smem_addr(&wbars[2 * NQ + i]), 2 * NH); // window empty: the tap warps
         }
         *abort_flag = 0;
-        for (int i = 0; i < kMixMaxStages; ++i) {
-            relcnt[i] = 0;
-            last_issued[i] = -1;
-        }
+        for (int i = 0; i < kMixMaxStages; ++i) last_issued[i] = -1;
         mbar_fence_init();
     }
     if (warp == 0) {
@@ -367,9 +344,9 @@ __global__ void __launch_bounds__(NW * 32, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc_fence_before();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
     const int64_t u_begin = a.part.first(blockIdx.x);
@@ -397,130 +374,140 @@ __global__ void __launch_bounds__(NW * 32, 1)
                       rbuf + (size_t)st * a.rec_bytes, smem_addr(&bars[st]), lane);
         if (lane == 0) last_issued[st] = k;
     };
-    // A warp is done with unit k (at position p, stage st, phase parity ph): arrive on the
-    // stage's empty barrier; the last of the NW warps to arrive refills the stage with unit
-    // k + stages at once.  Returns false on a timeout.
-    auto release = [&](int k, UnitPos p, int st, uint32_t ph) {
+    // A compute warp is done with the stage st of its current unit (every read of it issued
+    // and complete): one arrive per compute warp on the stage's empty barrier.
+    auto release = [&](int st) {
         __syncwarp();
-        int last = 0;
-        if (lane == 0) {
-            mbar_arrive(smem_addr(&bars[stages + st]));
-            last = atomicAdd(&relcnt[st], 1) == NW - 1;
-        }
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (!last) return true;
-        if (lane == 0) relcnt[st] = 0;
-        if (k + stages >= n_units) return true;
-        // every warp has arrived: the phase completes (its acquire orders their reads of the
-        // stage before the copy that overwrites it)
-        if (!mbar_wait_bounded(smem_addr(&bars[stages + st]), ph, abort_flag, a.status))
-            return false;
-        p.advance(stages, a.n_src);
-        issue(k + stages, p, st);
-        return true;
+        if (lane == 0) mbar_arrive(smem_addr(&bars[stages + st]));
     };
 
-    if (n_units > 0) {
-        // ---- compute: warp (q, ear) ----
-        const int q = warp & (NQ - 1), ear = warp / NQ;
+    if (n_units > 0 && warp == NW - 1) {
+        // ---- producer: fills the ring, then refills each stage as soon as the NC compute
+        // warps have released it, with the unit `stages` ahead ----
+        UnitPos p = pos0;
+        for (int k0 = 0; k0 < n_units && k0 < stages; ++k0) {
+            issue(k0, p, k0);
+            p.advance(1, a.n_src);
+        }
+        int st = 0;
+        uint32_t ph = 0;
+        for (int r = 0; r + stages < n_units; ++r) {
+            if (!mbar_wait_bounded(smem_addr(&bars[stages + st]), ph, abort_flag, a.status)) break;
+            issue(r + stages, p, st);
+            p.advance(1, a.n_src);
+            if (++st == stages) {
+                st = 0;
+                ph ^= 1u;
+            }
+        }
+    } else if (n_units > 0) {
+        const int q = warp & (NQ - 1);
         const uint32_t tq = tmem_base + ((uint32_t)(32 * q) << 16);
         const int lane_off = (q * 32 + lane) * R;
         const int n_seg = a.nseg;
         const int64_t n_steps = (int64_t)n_units * n_seg;
-        uint64_t acc[RP];
-#pragma unroll
-        for (int i = 0; i < RP; ++i) acc[i] = 0;
-        int slot = a.part.slot_base(blockIdx.x, pos0.t), run_n = 0;
+        const uint32_t win_full = smem_addr(&wbars[q * 2]);           // + 8 * buffer
+        const uint32_t win_empty = smem_addr(&wbars[2 * NQ + q * 2]);  // + 8 * buffer
 
-        // the window of a step (stage st, segment seg) for this warp's half
-        auto window_src = [&](int st, int seg) {
-            return ybuf + (size_t)st * a.buf_elems + a.halo + lane_off - (seg + 1) * SW + kHalf * ear;
-        };
-        // prologue: fill the ring, the first window into buffer 0
-        if (warp == 0) {
-            UnitPos p = pos0;
-            for (int k0 = 0; k0 < n_units && k0 < stages; ++k0) {
-                issue(k0, p, k0);
-                p.advance(1, a.n_src);
-            }
-        }
-        bool ok = mbar_wait_bounded(smem_addr(&bars[0]), 0u, abort_flag, a.status);
-        if (ok) copy_half<T>(window_src(0, 0), tq + (uint32_t)(kHalf * ear));
-        tm_wait_st();
-        ok = pair_sync_all(q, ok);
-
-        // current step: unit k at position pos, stage st, parity ph; segment seg
-        int k = 0, st = 0, seg = 0, toff = 0;
+        // step j: unit k at position pos, stage st with phase parity ph, segment seg; window
+        // buffer j & 1, used for the (j >> 1)-th time
+        int k = 0, st = 0, seg = 0;
         uint32_t ph = 0;
         UnitPos pos = pos0;
-        for (int64_t j = 0; ok && j < n_steps; ++j) {
-            // next step
-            const bool last_seg = seg == n_seg - 1;
-            const int k1 = last_seg ? k + 1 : k;
-            const int seg1 = last_seg ? 0 : seg + 1;
-            int st1 = st;
-            uint32_t ph1 = ph;
-            if (last_seg && ++st1 == stages) {
-                st1 = 0;
-                ph1 ^= 1u;
-            }
-            const bool have_next = k1 < n_units;
-            bool ok_next = true;
-            if (have_next && last_seg)
-                ok_next = mbar_wait_bounded(smem_addr(&bars[st1]), ph1, abort_flag, a.status);
-            // the next window's half: the left-ear warp copies it before its taps, the
-            // right-ear warp after them, so that on their shared SM sub-partition one warp's
-            // copy overlaps the other's FMAs
-            const bool copy = have_next && ok_next;
-            const T *nsrc = window_src(copy ? st1 : st, copy ? seg1 : seg);
-            const uint32_t ndst = tq + (uint32_t)(kCols * ((j + 1) & 1) + kHalf * ear);
-            if (copy && ear == 0) copy_half<T>(nsrc, ndst);
-            // taps of this warp's ear in segment seg of unit k
-            const unsigned char *rec = rbuf + (size_t)st * a.rec_bytes;
-            const int2 c = reinterpret_cast<const int2 *>(rec + 16)[seg];
-            const int2 *taps = reinterpret_cast<const int2 *>(rec + 16 + 8 * a.nchunk) + toff +
-                               (ear ? c.x : 0);
-            apply_taps(acc, tq + (uint32_t)(kCols * (j & 1)), taps, ear ? c.y : c.x);
-            toff += c.x + c.y;
-            if (last_seg && !release(k, pos, st, ph)) ok_next = false;   // last read of unit k's stage
-            if (copy && ear == 1) copy_half<T>(nsrc, ndst);
-            tm_wait_st();
-            ok = pair_sync_all(q, ok_next);
-            if (last_seg) {
-                // unit k done: flush the run at its end
-                ++run_n;
-                const bool tile_end = (k + 1 == n_units) || (pos.s + 1 == a.n_src);
-                if (run_n == a.part.gs || tile_end) {
-                    float4 *p = reinterpret_cast<float4 *>(
-                        a.partial + ((size_t)pos.t * a.slots + slot) * 2 * kTile + ear * kTile + lane_off);
-#pragma unroll
-                    for (int i = 0; i < R / 4; ++i) {
-                        float x0, x1, x2, x3;
-                        asm("mov.b64 {%0, %1}, %2;" : "=f"(x0), "=f"(x1) : "l"(acc[2 * i]));
-                        asm("mov.b64 {%0, %1}, %2;" : "=f"(x2), "=f"(x3) : "l"(acc[2 * i + 1]));
-                        p[i] = make_float4(x0, x1, x2, x3);
+        if (warp >= NTW) {
+            // ---- copy warp of lane quarter q ----
+            for (int64_t j = 0; j < n_steps; ++j) {
+                const uint32_t buf = (uint32_t)j & 1u;
+                if (seg == 0 && !mbar_wait_bounded(smem_addr(&bars[st]), ph, abort_flag, a.status))
+                    break;
+                if (j >= 2 && !mbar_wait_bounded(win_empty + 8 * buf, (uint32_t)((j >> 1) - 1) & 1u,
+                                                 abort_flag, a.status))
+                    break;
+                tc_fence_after();
+                copy_window<T>(ybuf + (size_t)st * a.buf_elems + a.halo + lane_off - (seg + 1) * SW,
+                               tq + kCols * buf);
+                tm_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(win_full + 8 * buf);
+                if (seg == n_seg - 1) {
+                    release(st);                              // last read of unit k's stage
+                    pos.advance(1, a.n_src);
+                    ++k;
+                    seg = 0;
+                    if (++st == stages) {
+                        st = 0;
+                        ph ^= 1u;
                     }
-#pragma unroll
-                    for (int i = 0; i < RP; ++i) acc[i] = 0;
-                    ++slot;
-                    run_n = 0;
-                }
-                toff = 0;
-                pos.advance(1, a.n_src);
-                if (tile_end && k1 < n_units) {
-                    slot = a.part.slot_base(blockIdx.x, pos.t);   // the next tile's first slot
-                    run_n = 0;
+                } else {
+                    ++seg;
                 }
             }
-            k = k1;
-            seg = seg1;
-            st = st1;
-            ph = ph1;
+        } else {
+            // ---- tap warp (lane quarter q, ear, half): outputs [RS half, RS half + RS) of
+            // each lane ----
+            const int ear = (warp / NQ) & 1, half = warp / (2 * NQ);
+            uint64_t acc[RP];
+#pragma unroll
+            for (int i = 0; i < RP; ++i) acc[i] = 0;
+            int slot = a.part.slot_base(blockIdx.x, pos0.t), run_n = 0, toff = 0;
+            for (int64_t j = 0; j < n_steps; ++j) {
+                const uint32_t buf = (uint32_t)j & 1u;
+                if (seg == 0 && !mbar_wait_bounded(smem_addr(&bars[st]), ph, abort_flag, a.status))
+                    break;
+                if (!mbar_wait_bounded(win_full + 8 * buf, (uint32_t)(j >> 1) & 1u, abort_flag, a.status))
+                    break;
+                tc_fence_after();
+                // taps of this warp's ear in segment seg of unit k
+                const unsigned char *rec = rbuf + (size_t)st * a.rec_bytes;
+                const int2 c = reinterpret_cast<const int2 *>(rec + 16)[seg];
+                const int2 *taps = reinterpret_cast<const int2 *>(rec + 16 + 8 * a.nchunk) + toff +
+                                   (ear ? c.x : 0);
+                apply_taps(acc, tq + kCols * buf + RS * half, taps, ear ? c.y : c.x);  // ends with wait::ld
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(win_empty + 8 * buf);
+                toff += c.x + c.y;
+                if (seg == n_seg - 1) {
+                    release(st);                              // last read of unit k's stage
+                    // unit k done: flush the run at its end
+                    ++run_n;
+                    const bool tile_end = (k + 1 == n_units) || (pos.s + 1 == a.n_src);
+                    if (run_n == a.part.gs || tile_end) {
+                        float2 *p = reinterpret_cast<float2 *>(a.partial + ((size_t)pos.t * a.slots + slot) * 2 * kTile +
+                                                               ear * kTile + lane_off + RS * half);
+#pragma unroll
+                        for (int i = 0; i < RP; ++i) {
+                            float x0, x1;
+                            asm("mov.b64 {%0, %1}, %2;" : "=f"(x0), "=f"(x1) : "l"(acc[i]));
+                            p[i] = make_float2(x0, x1);
+                        }
+#pragma unroll
+                        for (int i = 0; i < RP; ++i) acc[i] = 0;
+                        ++slot;
+                        run_n = 0;
+                    }
+                    toff = 0;
+                    pos.advance(1, a.n_src);
+                    ++k;
+                    seg = 0;
+                    if (++st == stages) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
+                    if (tile_end && k < n_units) {
+                        slot = a.part.slot_base(blockIdx.x, pos.t);   // the next tile's first slot
+                        run_n = 0;
+                    }
+                } else {
+                    ++seg;
+                }
+            }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc_fence_before();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc_fence_after();
     if (warp == 0) {
         // let every copy still in flight land before the CTA exits (bounded; immediate unless
         // a wait timed out): the last unit issued into each stage

@@ -130,7 +130,9 @@ def _moving_case(rng, S, L, seg, k, n_dirs=40):
 
 
 @pytest.mark.parametrize("S,L,seg,k", [(5, 3000, 256, 16), (3, 1000, 128, 8), (70, 20001, 256, 16),
-                                       (2, 5000, 1024, 32), (1, 100, 256, 16)])
+                                       (2, 5000, 1024, 32), (1, 100, 256, 16),
+                                       # k_max not a multiple of 4: tables staged by lane copies
+                                       (4, 2999, 128, 6), (2, 1537, 640, 5)])
 def test_moving_render_matches_oracle(rend, S, L, seg, k):
     from paper_1502_03162_gb300 import hrir
     rng = np.random.default_rng(S * 31 + L)
