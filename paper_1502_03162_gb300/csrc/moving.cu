@@ -88,27 +88,40 @@ struct MovLayout {
     }
 };
 
-// Segments whose filters a tile starting at output t0 uses: rows [j_lo, j_lo + n_rows) of the
-// tables (the previous segment's filter for the crossfade, clamped to the table).
-struct SegRange {
-    int j_lo, n_rows;
-    __device__ SegRange(const MovingArgs &a, int t0)
+// What a tile of outputs [t0, t0 + kTile) needs of the per-segment tables, computed once per
+// tile (units are tile-major, so it changes once every n_src units): table rows
+// [j_lo, j_lo + n_rows) (the previous segment's filter for the crossfade, clamped to the
+// table), the merged lists [p_lo, p_hi) its outputs use (2 per segment: ears), and for the
+// calling warp's 128 outputs their segment jw, its row jc and whether they crossfade.
+struct TileInfo {
+    int j_lo, n_rows, p_lo, p_hi, jw, jc;
+    bool fade;
+    __device__ TileInfo(const MovingArgs &a, int t, int warp)
     {
+        const int t0 = t * kTile;
+        const int last = a.n_seg - 1;
         int jl = t0 / a.seg_len - 1;
         jl = jl < 0 ? 0 : jl;
-        j_lo = jl < a.n_seg - 1 ? jl : a.n_seg - 1;
-        const int j_hi = j_lo + a.n_js - 1 < a.n_seg - 1 ? j_lo + a.n_js - 1 : a.n_seg - 1;
+        j_lo = jl < last ? jl : last;
+        const int j_hi = j_lo + a.n_js - 1 < last ? j_lo + a.n_js - 1 : last;
         n_rows = j_hi - j_lo + 1;
+        const int jw_lo = t0 / a.seg_len, jw_hi = (t0 + kTile - 1) / a.seg_len;
+        p_lo = 2 * ((jw_lo < last ? jw_lo : last) - j_lo);
+        p_hi = 2 * ((jw_hi < last ? jw_hi : last) - j_lo) + 2;
+        jw = (t0 + 128 * warp) / a.seg_len;
+        const bool tail = jw >= a.n_seg;
+        jc = (tail ? last : jw) - j_lo;
+        fade = !tail && jw >= 1;
     }
 };
 
-// Tap counts of unit (tile t, source s), lane i holding count i (n_rows * 2 <= 20 lanes),
-// loaded one unit ahead of its staging so that their latency never stalls the issuing warp.
-__device__ __forceinline__ uint32_t load_counts(const MovingArgs &a, int t, int s, int lane)
+// Tap counts of a unit of source s in a tile with table rows from j_lo (n_rows of them), lane
+// i holding count i (n_rows * 2 <= 20 lanes), loaded one unit ahead of its staging so that
+// their latency never stalls the issuing warp.
+__device__ __forceinline__ uint32_t load_counts(const MovingArgs &a, const TileInfo &ti, int s, int lane)
 {
-    const SegRange sr(a, t * kTile);
-    const int64_t row0 = (int64_t)s * a.n_seg + sr.j_lo;
-    return lane < sr.n_rows * 2 ? (uint32_t)a.tap_nnz[row0 * 2 + lane] : 0u;
+    const int64_t row0 = (int64_t)s * a.n_seg + ti.j_lo;
+    return lane < ti.n_rows * 2 ? (uint32_t)a.tap_nnz[row0 * 2 + lane] : 0u;
 }
 
 // Stage unit (tile t, source s) (all lanes of warp 0): the raw window y[x0, x0 + raw) with
@@ -117,7 +130,8 @@ __device__ __forceinline__ uint32_t load_counts(const MovingArgs &a, int t, int 
 // they are 16-byte aligned, else by lane copies; the counts (loaded earlier, `counts`) by
 // lane stores.  The lane stores come before the arrive that publishes them.
 __device__ __forceinline__ void issue_unit(const MovingArgs &a, const MovLayout &L, unsigned char *stage,
-                                           uint32_t bar, int t, int s, uint32_t counts, int lane)
+                                           uint32_t bar, int t, const TileInfo &sr, int s, uint32_t counts,
+                                           int lane)
 {
     const int t0 = t * kTile;                       // < 2^31: len < 2^31
     const int64_t x0 = (int64_t)t0 - a.halo;        // a multiple of 4
@@ -133,7 +147,6 @@ __device__ __forceinline__ void issue_unit(const MovingArgs &a, const MovLayout 
         const int64_t p = x0 + i;
         raw[i] = (p >= 0 && p < a.len) ? __ldg(ys + p) : 0.f;
     }
-    const SegRange sr(a, t0);
     const int64_t row0 = (int64_t)s * a.n_seg + sr.j_lo;
     const int n_ent = sr.n_rows * 2 * a.k_max;
     uint16_t *idx = reinterpret_cast<uint16_t *>(stage + L.st_idx);
@@ -184,17 +197,19 @@ __global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArg
     int s = (int)(u_begin - (int64_t)t * a.n_src);
     int it = t, is = s;                                   // position of the next unit to issue
     int issued = 0;
+    TileInfo ti_issue(a, it, warp);                       // of tile it
     uint32_t counts = 0;                                  // its tap counts (warp 0)
-    if (warp == 0 && n_units > 0) counts = load_counts(a, it, is, lane);
+    if (warp == 0 && n_units > 0) counts = load_counts(a, ti_issue, is, lane);
     auto issue_next = [&]() {
         issue_unit(a, L, smem + (size_t)(issued % kStages) * L.stage, smem_addr(&bars[issued % kStages]),
-                   it, is, counts, lane);
+                   it, ti_issue, is, counts, lane);
         ++issued;
         if (++is == a.n_src) {
             is = 0;
             ++it;
+            ti_issue = TileInfo(a, it, warp);
         }
-        if (issued < n_units) counts = load_counts(a, it, is, lane);
+        if (issued < n_units) counts = load_counts(a, ti_issue, is, lane);
     };
     if (warp == 0)
         while (issued < n_units && issued < kStages) issue_next();
@@ -206,6 +221,7 @@ __global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArg
         for (int r = 0; r < kPer; ++r) zr[e][r] = 0.f;
     int slot = a.part.slot_base(blockIdx.x, t), run_n = 0;
     const float inv_seg = 1.0f / (float)a.seg_len;      // crossfade slope
+    TileInfo sr(a, t, warp);                             // of the current unit's tile
     int st = 0;
     uint32_t ph = 0;
     int k = 0;
@@ -216,7 +232,6 @@ __global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArg
         const int row = 2 * a.k_max;                      // merged-list capacity per (segment, ear)
         int4 *ml = reinterpret_cast<int4 *>(smem + L.ml) + b * a.n_js * 2 * row;
         int *mcnt = reinterpret_cast<int *>(smem + L.mcnt) + b * a.n_js * 2;
-        const SegRange sr(a, t0);
         // ---- build unit k: shifted copies Y[c][q] = y[t0 - halo + q + c], merged tap lists ----
         bool ok = mbar_wait_bounded(smem_addr(&bars[st]), ph, abort_flag, a.status);
         if (ok) {
@@ -240,10 +255,7 @@ __global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArg
             const float *w = reinterpret_cast<const float *>(stage + L.st_w);
             const uint8_t *nnz = stage + L.st_nnz;
             uint8_t *lut_base = smem + L.lut;
-            const int jw_lo = t0 / a.seg_len, jw_hi = (t0 + kTile - 1) / a.seg_len;
-            const int p_lo = 2 * ((jw_lo < a.n_seg - 1 ? jw_lo : a.n_seg - 1) - sr.j_lo);
-            const int p_hi = 2 * ((jw_hi < a.n_seg - 1 ? jw_hi : a.n_seg - 1) - sr.j_lo) + 2;
-            for (int p = p_lo + warp; p < p_hi; p += kThreads / 32) {
+            for (int p = sr.p_lo + warp; p < sr.p_hi; p += kThreads / 32) {
                 const int jc = p >> 1, e = p & 1;
                 const int jr = jc < sr.n_rows - 1 ? jc : sr.n_rows - 1;
                 const int jp = jc < 1 ? -1 : (jc - 1 < sr.n_rows - 1 ? jc - 1 : sr.n_rows - 1);
@@ -319,14 +331,10 @@ __global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArg
         }
 
         // ---- this warp's segment and crossfade ----
-        const int nw = t0 + 128 * warp;
-        const int jw = nw / a.seg_len;
-        const bool tail = jw >= a.n_seg;
-        const int jcur = tail ? a.n_seg - 1 : (int)jw;
-        const bool fade = !tail && jw >= 1;
+        const int jw = sr.jw, jc = sr.jc;
+        const bool fade = sr.fade;
         // this thread's first output in the shifted copies
         const char *yl = reinterpret_cast<const char *>(Y + kPer * tid + a.halo);
-        const int jc = jcur - sr.j_lo;
         const int n0 = t0 + kPer * tid;
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
@@ -390,6 +398,7 @@ __global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArg
             if (k + 1 < n_units) {
                 slot = a.part.slot_base(blockIdx.x, t);   // the next tile's first slot
                 run_n = 0;
+                sr = TileInfo(a, t, warp);
             }
         }
     }
