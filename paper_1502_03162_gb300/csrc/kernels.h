@@ -226,7 +226,6 @@ struct ResonanceArgs {
 };
 size_t resonance_gemm_smem_bytes(int elem_bytes);
 // tmap: 2-D tensor map over the 16-bit sources with box {256, 1}
-int resonance_gemm_ctas_per_sm(int dtype);   // resident CTAs per SM (>= 1)
 cudaError_t launch_resonance_gemm(int dtype, const CUtensorMap &tmap, const ResonanceArgs &a,
                                   int grid, cudaStream_t st);
 

@@ -36,7 +36,7 @@ int64_t act_stride(int refl_len) { return round_up(3 * H + refl_len, 4); }
 // Rows per forward chunk when the caller keeps no activations.
 constexpr int64_t kFwdChunk = 1 << 16;
 // Rows per chunk of the tensor-core inference (two BF16 activation buffers of 256 columns).
-constexpr int64_t kTcChunk = 1 << 19;
+constexpr int64_t kTcChunk = 1 << 22;
 
 int grow_ws(hrir_ctx *ctx, size_t need)
 {
@@ -393,7 +393,7 @@ int hrir_resonance_per_source(hrir_ctx *ctx, int n_src, int64_t len, int64_t src
     a.out_ld = out_ld;
     a.status = ctx->d_status;
     const int64_t units = ((out_len + kResTile - 1) / kResTile) * n_src;
-    const int grid = (int)std::min<int64_t>(units, (int64_t)ctx->num_sms * resonance_gemm_ctas_per_sm((int)dt));
+    const int grid = (int)std::min<int64_t>(units, (int64_t)ctx->num_sms * 4);
     KernelTimer kt(ctx, HRIR_K_RESONANCE, st);
     HRIR_CUDA_TRY(ctx, launch_resonance_gemm((int)dt, tmap, a, grid, st));
     kt.done();

@@ -10,7 +10,9 @@
 // N = 256 or Lg rounded up to 16) from one thread, commits to an mbarrier, and the 4 warps
 // read their 32 accumulator rows with tcgen05.ld and apply bias + ReLU (hidden layers,
 // stored as BF16 for the next layer) or bias + softplus (output layer, stored as FP32).
-// Waits are bounded.
+// For layers 3 and 4 the next tile's input rows are loaded into registers (each warp one
+// 512-byte row per step, coalesced) while the MMAs and the epilogue of the current tile run,
+// and stored into the A operand after it.  Waits are bounded.
 #include <cuda_bf16.h>
 
 #include "kernels.h"
@@ -72,7 +74,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
     uint64_t *bar = reinterpret_cast<uint64_t *>(Am + kRows * kK);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
     int *abort_flag = reinterpret_cast<int *>(bar + 1) + 1;
-    float *w1 = reinterpret_cast<float *>(bar + 2);                      // layer 2: W1 [256][5], b1 [256]
+    float *bias = reinterpret_cast<float *>(bar + 2);                    // [256] this layer's biases
+    float *w1 = bias + kK;                                               // layer 2: W1 [256][5], b1 [256]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -93,6 +96,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
         const float v = n < a.N ? a.W[(size_t)n * kK + k] : 0.f;
         Wm[core_off(n, k)] = __float2bfloat16_rn(v);
     }
+    for (int i = tid; i < kK; i += kThreads) bias[i] = i < a.N ? a.b[i] : 0.f;
     if (a.first)
         for (int i = tid; i < kMlpHidden * (kMlpIn + 1); i += kThreads)
             w1[i] = i < kMlpHidden * kMlpIn ? a.W1[i] : a.b1[i - kMlpHidden * kMlpIn];
@@ -105,6 +109,28 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
     const uint32_t a_base = smem_addr(Am), w_base = smem_addr(Wm);
 
     const int64_t n_tiles = (a.n_rows + kRows - 1) / kRows;
+    // layers after the first: rows of a tile's input, step j = row 4 j + warp, lane = 16-byte
+    // chunk (kKc = 32 chunks a row)
+    static_assert(kKc == 32 && kRows % 4 == 0, "one row of chunks per warp and step");
+    constexpr int kSteps = kRows / 4;
+    uint4 pre[kSteps];
+    auto load_a = [&](int64_t t) {
+#pragma unroll
+        for (int j = 0; j < kSteps; ++j) {
+            const int64_t r = t * kRows + 4 * j + warp;
+            pre[j] = (t < n_tiles && r < a.n_rows) ? __ldg(reinterpret_cast<const uint4 *>(a.in + r * kK) + lane)
+                                                   : make_uint4(0, 0, 0, 0);
+        }
+    };
+    auto store_a = [&]() {
+#pragma unroll
+        for (int j = 0; j < kSteps; ++j)
+            *reinterpret_cast<uint4 *>(Am + core_off(4 * j + warp, lane * 8)) = pre[j];
+    };
+    if (!a.first) {
+        load_a(blockIdx.x);
+        store_a();
+    }
     uint32_t phase = 0;
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const int64_t r0 = t * kRows;
@@ -137,14 +163,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
                 }
                 *reinterpret_cast<uint4 *>(Am + core_off(tid, kc * 8)) = make_uint4(h[0], h[1], h[2], h[3]);
             }
-        } else {
-            for (int i = tid; i < kRows * kKc; i += kThreads) {
-                const int row = i / kKc, kc = i - row * kKc;
-                const int64_t r = r0 + row;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (r < a.n_rows) v = *reinterpret_cast<const uint4 *>(a.in + r * kK + kc * 8);
-                *reinterpret_cast<uint4 *>(Am + core_off(row, kc * 8)) = v;
-            }
         }
         fence_proxy_async_smem();
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -167,6 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
                     smem_addr(bar))
                 : "memory");
         }
+        if (!a.first) load_a(t + gridDim.x);          // in flight during the MMAs and the epilogue
         const bool ok = mbar_wait_bounded(smem_addr(bar), phase, abort_flag, a.status);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         phase ^= 1;
@@ -182,13 +201,13 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
                     float *o = a.out + r * a.N;
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        if (c0 + j < a.N) o[c0 + j] = softplus_f(__uint_as_float(v[j]) + a.b[c0 + j]);
+                        if (c0 + j < a.N) o[c0 + j] = softplus_f(__uint_as_float(v[j]) + bias[c0 + j]);
                 } else {
                     uint32_t h[16];
 #pragma unroll
                     for (int j = 0; j < 32; j += 2)
-                        h[j / 2] = pack_bf16(fmaxf(__uint_as_float(v[j]) + a.b[c0 + j], 0.f),
-                                             fmaxf(__uint_as_float(v[j + 1]) + a.b[c0 + j + 1], 0.f));
+                        h[j / 2] = pack_bf16(fmaxf(__uint_as_float(v[j]) + bias[c0 + j], 0.f),
+                                             fmaxf(__uint_as_float(v[j + 1]) + bias[c0 + j + 1], 0.f));
                     uint4 *o = reinterpret_cast<uint4 *>(a.hout + r * kK + c0);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) o[j] = make_uint4(h[4 * j], h[4 * j + 1], h[4 * j + 2], h[4 * j + 3]);
@@ -199,6 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
         __syncthreads();   // A and the accumulator are reused by the next tile
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!ok) break;
+        if (!a.first) store_a();                      // the next tile's A (made visible below)
     }
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
@@ -209,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
 
 size_t mlp_tc_smem_bytes(int n_pad)
 {
-    return (size_t)(n_pad + kRows) * kK * 2 + 16 + (size_t)kMlpHidden * (kMlpIn + 1) * 4;
+    return (size_t)(n_pad + kRows) * kK * 2 + 16 + (size_t)kK * 4 + (size_t)kMlpHidden * (kMlpIn + 1) * 4;
 }
 
 cudaError_t launch_mlp_layer_tc(const MlpTcArgs &a, int grid, cudaStream_t st)

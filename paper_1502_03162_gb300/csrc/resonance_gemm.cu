@@ -260,25 +260,6 @@ size_t resonance_gemm_smem_bytes(int elem_bytes)
     return (size_t)(kN * kK + kRows * kKA + kWin) * elem_bytes + 2 * 8 + 16;
 }
 
-// CTAs of the kernel resident per SM (>= 1): the grid-stride loop gives every CTA the same
-// share of the units, so a grid larger than one resident wave leaves a second, partial wave.
-int resonance_gemm_ctas_per_sm(int dtype)
-{
-    const size_t smem = resonance_gemm_smem_bytes(2);
-    int nb = 0;
-    cudaError_t e;
-    if (dtype == 1) {
-        auto k = resonance_gemm_kernel<__nv_bfloat16>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, smem);
-    } else {
-        auto k = resonance_gemm_kernel<__half>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, smem);
-    }
-    return (e == cudaSuccess && nb > 0) ? nb : 1;
-}
-
 cudaError_t launch_resonance_gemm(int dtype, const CUtensorMap &tmap, const ResonanceArgs &a, int grid,
                                   cudaStream_t st)
 {

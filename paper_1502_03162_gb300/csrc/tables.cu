@@ -9,29 +9,31 @@ namespace hrir {
 
 namespace {
 
-// ---- top-K: one warp per row ---------------------------------------------------------------
+// ---- top-K: one warp per row at a time ---------------------------------------------------
 // Keeps the k largest strictly positive entries (ties -> smaller index), emitted in ascending
 // index order, padded with (0, 0).  Lane l holds the contiguous slice [l*per, (l+1)*per) in
 // MAXPER registers (the smallest of 8, 16, 32, 64 that holds per = ceil(refl_len / 32)).
+// Persistent: each warp walks rows row0, row0 + n_warps, ... and loads the next row's slice
+// while it selects from the current one.
 constexpr int kTopkMaxPer = 64;  // refl_len <= 32 * 64 = 2048
 
 template <int MAXPER>
-__global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, int n_rows,
-                                                   int refl_len, int k, uint16_t *__restrict__ idx,
-                                                   float *__restrict__ w, uint8_t *__restrict__ nnz)
+__device__ __forceinline__ void topk_load(const float *__restrict__ g, int row, int n_rows, int refl_len,
+                                          int per, int j0, float (&v)[MAXPER])
 {
-    const int row = blockIdx.x * 4 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (row >= n_rows) return;
-    const int per = (refl_len + 31) / 32;
-    const int j0 = lane * per;
     const float *gr = g + (size_t)row * refl_len;
-    float v[MAXPER];
 #pragma unroll
     for (int j = 0; j < MAXPER; ++j) {
         const int gi = j0 + j;
-        v[j] = (j < per && gi < refl_len) ? gr[gi] : 0.0f;  // 0 is never selected
+        v[j] = (row < n_rows && j < per && gi < refl_len) ? __ldg(gr + gi) : 0.0f;  // 0 is never selected
     }
+}
+
+template <int MAXPER>
+__device__ __forceinline__ void topk_row(const float (&v)[MAXPER], int row, int j0, int lane, int k,
+                                         uint16_t *__restrict__ idx, float *__restrict__ w,
+                                         uint8_t *__restrict__ nnz)
+{
     // Each lane keeps its best remaining candidate as a key: the bits of a strictly positive
     // float order like the float, 0 = none; on equal keys the smaller position (strict >).  A
     // pick is the warp maximum of the keys, then the smallest index among the lanes holding
@@ -89,6 +91,26 @@ __global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, 
         rw[t] = 0.f;
     }
     if (lane == 0) nnz[row] = (uint8_t)cnt;
+}
+
+template <int MAXPER>
+__global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, int n_rows,
+                                                   int refl_len, int k, uint16_t *__restrict__ idx,
+                                                   float *__restrict__ w, uint8_t *__restrict__ nnz)
+{
+    const int lane = threadIdx.x & 31;
+    const int n_warps = gridDim.x * 4;
+    const int per = (refl_len + 31) / 32;
+    const int j0 = lane * per;
+    int row = blockIdx.x * 4 + (threadIdx.x >> 5);
+    float v[MAXPER], vn[MAXPER];
+    topk_load<MAXPER>(g, row, n_rows, refl_len, per, j0, v);
+    for (; row < n_rows; row += n_warps) {
+        topk_load<MAXPER>(g, row + n_warps, n_rows, refl_len, per, j0, vn);   // in flight
+        topk_row<MAXPER>(v, row, j0, lane, k, idx, w, nnz);
+#pragma unroll
+        for (int j = 0; j < MAXPER; ++j) v[j] = vn[j];
+    }
 }
 
 // ---- sparse records ------------------------------------------------------------------------
@@ -176,11 +198,21 @@ cudaError_t launch_topk(const float *g, int n_rows, int refl_len, int k, uint16_
     if (n_rows <= 0) return cudaSuccess;
     if (refl_len > 32 * kTopkMaxPer) return cudaErrorInvalidValue;
     const int per = (refl_len + 31) / 32;
-    const unsigned blocks = (unsigned)((n_rows + 3) / 4);
-    if (per <= 8) topk_kernel<8><<<blocks, 128, 0, st>>>(g, n_rows, refl_len, k, idx, w, nnz);
-    else if (per <= 16) topk_kernel<16><<<blocks, 128, 0, st>>>(g, n_rows, refl_len, k, idx, w, nnz);
-    else if (per <= 32) topk_kernel<32><<<blocks, 128, 0, st>>>(g, n_rows, refl_len, k, idx, w, nnz);
-    else topk_kernel<64><<<blocks, 128, 0, st>>>(g, n_rows, refl_len, k, idx, w, nnz);
+    // persistent warps: one resident wave of 4-warp blocks, fewer for small inputs
+    auto launch = [&](auto kern) {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        const int64_t need = ((int64_t)n_rows + 3) / 4, wave = (int64_t)sms * per_sm;
+        kern<<<(unsigned)(need < wave ? need : wave), 128, 0, st>>>(g, n_rows, refl_len, k, idx, w, nnz);
+    };
+    if (per <= 8) launch(topk_kernel<8>);
+    else if (per <= 16) launch(topk_kernel<16>);
+    else if (per <= 32) launch(topk_kernel<32>);
+    else launch(topk_kernel<64>);
     return cudaGetLastError();
 }
 

@@ -48,6 +48,21 @@ def test_topk_pack_bit_exact(rend, refl_len):
         np.testing.assert_array_equal(w.cpu().numpy().view(np.uint32), rw.view(np.uint32))
 
 
+@pytest.mark.parametrize("n_rows,refl_len", [(40000, 200), (20000, 1000)])
+def test_topk_pack_many_rows_bit_exact(rend, n_rows, refl_len):
+    """More rows than one resident wave of warps: every warp walks several rows."""
+    rng = np.random.default_rng(n_rows + refl_len)
+    G = rng.random((n_rows, refl_len), dtype=np.float32)
+    G[rng.random((n_rows, refl_len)) < 0.5] = 0.0
+    G[::7, :] = np.float32(0.5)                          # ties everywhere in some rows
+    idx, w, nnz = rend.topk_pack(_dev(G), 16)
+    torch.cuda.synchronize()
+    ri, rw, rn = oracle.topk(G, 16)
+    np.testing.assert_array_equal(nnz.cpu().numpy(), rn)
+    np.testing.assert_array_equal(idx.cpu().numpy().astype(np.int64) & 0xFFFF, ri.astype(np.int64))
+    np.testing.assert_array_equal(w.cpu().numpy().view(np.uint32), rw.view(np.uint32))
+
+
 # ------------------------------------------------------------------------------ rendering
 MODES = ("sparse", "dense", "fft")
 
