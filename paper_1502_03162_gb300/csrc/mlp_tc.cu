@@ -3,16 +3,16 @@
 // (source, segment, ear) rows of moving sources.
 //
 // One kernel per layer l = 2, 3, 4:  Z[r][n] = sum_k H[r][k] W_l[n][k] + b_l[n] (K = 256),
-// H = relu(z_{l-1}).  Each CTA (persistent over 128-row tiles) keeps W_l in shared memory in
-// the canonical no-swizzle K-major layout (8-row x 16-byte core matrices) and, per tile,
-// builds the A operand (for layer 2 straight from the features: z1 = W1 x + b1, ReLU, so
-// layer 1 is fused on the CUDA cores), issues 16 tcgen05.mma (K = 16 each, M = 128,
-// N = 256 or Lg rounded up to 16) from one thread, commits to an mbarrier, and the 4 warps
-// read their 32 accumulator rows with tcgen05.ld and apply bias + ReLU (hidden layers,
-// stored as BF16 for the next layer) or bias + softplus (output layer, stored as FP32).
-// For layers 3 and 4 the next tile's input rows are loaded into registers (each warp one
-// 512-byte row per step, coalesced) while the MMAs and the epilogue of the current tile run,
-// and stored into the A operand after it.  Waits are bounded.
+// H = relu(z_{l-1}).  Each CTA (8 warps, persistent over 128-row tiles) keeps W_l in shared
+// memory in the canonical no-swizzle K-major layout (8-row x 16-byte core matrices).  Per tile
+// it builds the A operand (for layer 2 straight from the features: z1 = W1 x + b1, ReLU, so
+// layer 1 is fused on the CUDA cores; for layers 3 and 4 from the previous layer's rows, which
+// were loaded into registers during the previous tile), one thread issues 16 tcgen05.mma
+// (K = 16 each, M = 128, N = 256 or Lg rounded up to 16) into one of two TMEM accumulators and
+// commits to an mbarrier, and while those MMAs run the 8 warps apply the epilogue of the
+// previous tile from the other accumulator: warp (lane quarter q, column half) reads its 32
+// rows with tcgen05.ld and applies bias + ReLU (hidden layers, stored as BF16 for the next
+// layer) or bias + softplus (output layer, stored as FP32).  Waits are bounded.
 #include <cuda_bf16.h>
 
 #include "kernels.h"
@@ -24,8 +24,9 @@ namespace {
 constexpr int kRows = 128;                  // MMA M: rows per tile
 constexpr int kK = kMlpHidden;              // 256
 constexpr int kKc = kK / 8;                 // core matrices along K
-constexpr int kThreads = 128;
-constexpr uint32_t kTmemCols = 256;
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr uint32_t kTmemCols = 512;         // two accumulators of 256 columns
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
@@ -91,80 +92,78 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     // this layer's weights (rows n >= N are zero) as BF16, canonical layout
-    for (int i = tid; i < a.n_pad * kK; i += kThreads) {
-        const int n = i / kK, k = i - n * kK;
-        const float v = n < a.N ? a.W[(size_t)n * kK + k] : 0.f;
-        Wm[core_off(n, k)] = __float2bfloat16_rn(v);
+    for (int i = tid; i < a.n_pad * kK / 4; i += kThreads) {
+        const int n = (4 * i) / kK, k = 4 * i - n * kK;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n < a.N) v = __ldg(reinterpret_cast<const float4 *>(a.W + (size_t)n * kK + k));
+        *reinterpret_cast<uint2 *>(Wm + core_off(n, k)) = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
     }
     for (int i = tid; i < kK; i += kThreads) bias[i] = i < a.N ? a.b[i] : 0.f;
     if (a.first)
         for (int i = tid; i < kMlpHidden * (kMlpIn + 1); i += kThreads)
             w1[i] = i < kMlpHidden * kMlpIn ? a.W1[i] : a.b1[i - kMlpHidden * kMlpIn];
-    fence_proxy_async_smem();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const uint32_t idesc = instr_desc_bf16(kRows, (uint32_t)a.n_pad);
     const uint32_t a_base = smem_addr(Am), w_base = smem_addr(Wm);
-
     const int64_t n_tiles = (a.n_rows + kRows - 1) / kRows;
-    // layers after the first: rows of a tile's input, step j = row 4 j + warp, lane = 16-byte
-    // chunk (kKc = 32 chunks a row)
-    static_assert(kKc == 32 && kRows % 4 == 0, "one row of chunks per warp and step");
-    constexpr int kSteps = kRows / 4;
+
+    // ---- A operand of tile t ----
+    // layers after the first: step j = row kWarps j + warp, lane = 16-byte chunk (kKc = 32
+    // chunks a row), loaded into registers one tile ahead
+    static_assert(kKc == 32 && kRows % kWarps == 0, "one row of chunks per warp and step");
+    constexpr int kSteps = kRows / kWarps;
     uint4 pre[kSteps];
     auto load_a = [&](int64_t t) {
 #pragma unroll
         for (int j = 0; j < kSteps; ++j) {
-            const int64_t r = t * kRows + 4 * j + warp;
+            const int64_t r = t * kRows + kWarps * j + warp;
             pre[j] = (t < n_tiles && r < a.n_rows) ? __ldg(reinterpret_cast<const uint4 *>(a.in + r * kK) + lane)
                                                    : make_uint4(0, 0, 0, 0);
         }
     };
-    auto store_a = [&]() {
+    // the first layer: row tid % 128, hidden units [128 h, 128 h + 128) with h = tid / 128:
+    // features, then relu(W1 x + b1)
+    auto build_a = [&](int64_t t) {
+        if (!a.first) {
 #pragma unroll
-        for (int j = 0; j < kSteps; ++j)
-            *reinterpret_cast<uint4 *>(Am + core_off(4 * j + warp, lane * 8)) = pre[j];
-    };
-    if (!a.first) {
-        load_a(blockIdx.x);
-        store_a();
-    }
-    uint32_t phase = 0;
-    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const int64_t r0 = t * kRows;
-        // ---- A operand: relu(previous layer) as BF16 ----
-        if (a.first) {
-            // row tid: features, then relu(W1 x + b1)
-            const int64_t r = r0 + tid;
-            float sa = 0.f, ca = 0.f, se = 0.f, ce = 0.f, ear = 0.f;
-            if (r < a.n_rows) {
-                const float *d = a.dirs + r * 3;
-                sincosf(d[0], &sa, &ca);
-                sincosf(d[1], &se, &ce);
-                ear = d[2];
-            }
-            const float x[kMlpIn] = {sa, ca, se, ce, ear};
-            for (int kc = 0; kc < kKc; ++kc) {
-                uint32_t h[4];
-#pragma unroll
-                for (int j = 0; j < 8; j += 2) {
-                    float z2[2];
-#pragma unroll
-                    for (int jj = 0; jj < 2; ++jj) {
-                        const int n = kc * 8 + j + jj;
-                        float z = w1[kMlpHidden * kMlpIn + n];
-#pragma unroll
-                        for (int q = 0; q < kMlpIn; ++q) z = fmaf(w1[n * kMlpIn + q], x[q], z);
-                        z2[jj] = r < a.n_rows ? fmaxf(z, 0.f) : 0.f;
-                    }
-                    h[j / 2] = pack_bf16(z2[0], z2[1]);
-                }
-                *reinterpret_cast<uint4 *>(Am + core_off(tid, kc * 8)) = make_uint4(h[0], h[1], h[2], h[3]);
-            }
+            for (int j = 0; j < kSteps; ++j)
+                *reinterpret_cast<uint4 *>(Am + core_off(kWarps * j + warp, lane * 8)) = pre[j];
+            return;
         }
-        fence_proxy_async_smem();
+        const int row = tid & (kRows - 1), h = tid / kRows;
+        const int64_t r = t * kRows + row;
+        float sa = 0.f, ca = 0.f, se = 0.f, ce = 0.f, ear = 0.f;
+        if (r < a.n_rows) {
+            const float *d = a.dirs + r * 3;
+            sincosf(d[0], &sa, &ca);
+            sincosf(d[1], &se, &ce);
+            ear = d[2];
+        }
+        const float x[kMlpIn] = {sa, ca, se, ce, ear};
+        for (int kc = h * kKc / 2; kc < (h + 1) * kKc / 2; ++kc) {
+            uint32_t hv[4];
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) {
+                float z2[2];
+#pragma unroll
+                for (int jj = 0; jj < 2; ++jj) {
+                    const int n = kc * 8 + j + jj;
+                    float z = w1[kMlpHidden * kMlpIn + n];
+#pragma unroll
+                    for (int q = 0; q < kMlpIn; ++q) z = fmaf(w1[n * kMlpIn + q], x[q], z);
+                    z2[jj] = r < a.n_rows ? fmaxf(z, 0.f) : 0.f;
+                }
+                hv[j / 2] = pack_bf16(z2[0], z2[1]);
+            }
+            *reinterpret_cast<uint4 *>(Am + core_off(row, kc * 8)) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        }
+    };
+    // one thread issues the MMAs of the tile in A into accumulator buffer b, then commits
+    auto issue_mma = [&](uint32_t b) {
+        fence_proxy_async_smem();     // A's generic stores before the MMAs read it
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -176,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
                 const uint32_t acc = ks > 0 ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + b * 256u),
                     "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
                     : "memory");
             }
@@ -185,41 +184,82 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
                     smem_addr(bar))
                 : "memory");
         }
-        if (!a.first) load_a(t + gridDim.x);          // in flight during the MMAs and the epilogue
-        const bool ok = mbar_wait_bounded(smem_addr(bar), phase, abort_flag, a.status);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        phase ^= 1;
-        // ---- epilogue: lane = row ----
-        if (ok) {
-            const int row = warp * 32 + lane;
-            const int64_t r = r0 + row;
-            for (int c0 = 0; c0 < a.n_pad; c0 += 32) {
-                uint32_t v[32];
-                tm_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-                if (r >= a.n_rows) continue;
-                if (a.last) {
-                    float *o = a.out + r * a.N;
+    };
+    // epilogue of tile t from accumulator buffer b: warp (lane quarter warp % 4) takes the
+    // 32-column chunks c of parity warp / 4
+    auto epilogue = [&](int64_t t, uint32_t b) {
+        const int q = warp & 3, half = warp >> 2;
+        const int row = q * 32 + lane;
+        const int64_t r = t * kRows + row;
+        for (int c0 = 32 * half; c0 < a.n_pad; c0 += 64) {
+            uint32_t v[32];
+            tm_ld32(tmem + b * 256u + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+            if (r >= a.n_rows) continue;
+            if (a.last) {
+                float *o = a.out + r * a.N;
+                if ((a.N & 3) == 0 && ((uintptr_t)a.out & 15) == 0) {   // 16-byte aligned rows: vector stores
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4)
+                        if (c0 + j < a.N)
+                            *reinterpret_cast<float4 *>(o + c0 + j) = make_float4(
+                                softplus_f(__uint_as_float(v[j]) + bias[c0 + j]),
+                                softplus_f(__uint_as_float(v[j + 1]) + bias[c0 + j + 1]),
+                                softplus_f(__uint_as_float(v[j + 2]) + bias[c0 + j + 2]),
+                                softplus_f(__uint_as_float(v[j + 3]) + bias[c0 + j + 3]));
+                } else {
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
                         if (c0 + j < a.N) o[c0 + j] = softplus_f(__uint_as_float(v[j]) + bias[c0 + j]);
-                } else {
-                    uint32_t h[16];
-#pragma unroll
-                    for (int j = 0; j < 32; j += 2)
-                        h[j / 2] = pack_bf16(fmaxf(__uint_as_float(v[j]) + bias[c0 + j], 0.f),
-                                             fmaxf(__uint_as_float(v[j + 1]) + bias[c0 + j + 1], 0.f));
-                    uint4 *o = reinterpret_cast<uint4 *>(a.hout + r * kK + c0);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) o[j] = make_uint4(h[4 * j], h[4 * j + 1], h[4 * j + 2], h[4 * j + 3]);
                 }
+            } else {
+                uint32_t hv[16];
+#pragma unroll
+                for (int j = 0; j < 32; j += 2)
+                    hv[j / 2] = pack_bf16(fmaxf(__uint_as_float(v[j]) + bias[c0 + j], 0.f),
+                                          fmaxf(__uint_as_float(v[j + 1]) + bias[c0 + j + 1], 0.f));
+                uint4 *o = reinterpret_cast<uint4 *>(a.hout + r * kK + c0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) o[j] = make_uint4(hv[4 * j], hv[4 * j + 1], hv[4 * j + 2], hv[4 * j + 3]);
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();   // A and the accumulator are reused by the next tile
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!ok) break;
-        if (!a.first) store_a();                      // the next tile's A (made visible below)
+    };
+
+    // pipeline: the MMAs of tile t + 1 run while the epilogue of tile t reads the other
+    // accumulator
+    int64_t t = blockIdx.x;
+    uint32_t phase = 0, b = 0;
+    if (t < n_tiles) {
+        if (!a.first) load_a(t);
+        build_a(t);
+        issue_mma(0);
+        if (!a.first) load_a(t + gridDim.x);
     }
+    for (; t < n_tiles; t += gridDim.x) {
+        const bool ok = mbar_wait_bounded(smem_addr(bar), phase, abort_flag, a.status);   // MMAs of t
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        phase ^= 1;
+        if (!ok) break;
+        const int64_t tn = t + gridDim.x;
+        if (tn < n_tiles) {
+            build_a(tn);                            // A is free: the MMAs of t completed
+            issue_mma(b ^ 1u);
+            if (!a.first) load_a(tn + gridDim.x);   // in flight during the epilogue
+        }
+        epilogue(t, b);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();                            // buffer b is read before the MMAs of t + 2
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        b ^= 1u;
+    }
+    // MMAs still in flight after an expired wait: let them finish (bounded) before the dealloc
+    if (t < n_tiles) {
+        const uint64_t t0 = global_timer_ns();
+        while (!mbar_try_wait(smem_addr(bar), phase ^ 1u) && global_timer_ns() - t0 < kWaitLimitNs) {
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                      : "memory");

@@ -34,37 +34,78 @@ __device__ __forceinline__ void topk_row(const float (&v)[MAXPER], int row, int 
                                          uint16_t *__restrict__ idx, float *__restrict__ w,
                                          uint8_t *__restrict__ nnz)
 {
-    // Each lane keeps its best remaining candidate as a key: the bits of a strictly positive
-    // float order like the float, 0 = none; on equal keys the smaller position (strict >).  A
-    // pick is the warp maximum of the keys, then the smallest index among the lanes holding
-    // it; only the winning lane rescans its slice.
+    // Keys: the bits of a strictly positive float order like the float; 0 = not selectable.
+    // The selected set is every key above T plus the first ties at T in index order, where T
+    // is the k-th largest key: the largest t with #(key >= t) >= k, found by bisection over
+    // the key bits (warp-wide counts), stopping early when exactly k keys are >= t.
     using Mask = typename std::conditional<(MAXPER <= 32), uint32_t, uint64_t>::type;
-    Mask taken = 0;
-    uint32_t key = 0;
-    int pos = 0;
-    auto rescan = [&]() {
-        key = 0;
-        pos = 0;
+    uint32_t key[MAXPER];
+    int n_pos = 0;
+    uint32_t kmax = 0;
 #pragma unroll
-        for (int j = 0; j < MAXPER; ++j) {
-            const uint32_t b = __float_as_uint(v[j]);
-            if (!((taken >> j) & 1) && v[j] > 0.f && b > key) {
-                key = b;
-                pos = j;
+    for (int j = 0; j < MAXPER; ++j) {
+        key[j] = v[j] > 0.f ? __float_as_uint(v[j]) : 0u;
+        n_pos += key[j] != 0u;
+        kmax = key[j] > kmax ? key[j] : kmax;
+    }
+    auto count_ge = [&](uint32_t t) {
+        int c = 0;
+#pragma unroll
+        for (int j = 0; j < MAXPER; ++j) c += key[j] >= t;
+        return (int)__reduce_add_sync(0xffffffffu, (uint32_t)c);
+    };
+    const int total = (int)__reduce_add_sync(0xffffffffu, (uint32_t)n_pos);
+    Mask taken = 0;
+    int cnt;
+    if (total <= k) {                       // every positive entry
+#pragma unroll
+        for (int j = 0; j < MAXPER; ++j)
+            if (key[j]) taken |= (Mask)1 << j;
+        cnt = total;
+    } else {
+        uint32_t lo = 1, hi = __reduce_max_sync(0xffffffffu, kmax) + 1u;   // #(>= lo) >= k > #(>= hi)
+        bool exact = false;
+        while (hi - lo > 1u) {
+            const uint32_t mid = lo + (hi - lo) / 2u;
+            const int c = count_ge(mid);
+            if (c >= k) {
+                lo = mid;
+                if (c == k) {
+                    exact = true;
+                    break;
+                }
+            } else {
+                hi = mid;
             }
         }
-    };
-    rescan();
-    int cnt = 0;
-    for (; cnt < k; ++cnt) {
-        const uint32_t m = __reduce_max_sync(0xffffffffu, key);
-        if (m == 0) break;
-        const uint32_t cand = key == m ? (uint32_t)(j0 + pos) : 0xffffffffu;
-        const uint32_t win = __reduce_min_sync(0xffffffffu, cand);
-        if (cand == win) {
-            taken |= (Mask)1 << pos;
-            rescan();
+        if (exact) {
+#pragma unroll
+            for (int j = 0; j < MAXPER; ++j)
+                if (key[j] >= lo) taken |= (Mask)1 << j;
+        } else {
+            // lo is the k-th largest key: every key above it, then its ties in index order
+            int need = k - count_ge(lo + 1u);
+            int ties = 0;
+#pragma unroll
+            for (int j = 0; j < MAXPER; ++j) ties += key[j] == lo;
+            int before_t = ties;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int o = __shfl_up_sync(0xffffffffu, before_t, off);
+                if (lane >= off) before_t += o;
+            }
+            need -= before_t - ties;        // ties already taken by lower lanes
+#pragma unroll
+            for (int j = 0; j < MAXPER; ++j) {
+                if (key[j] > lo) {
+                    taken |= (Mask)1 << j;
+                } else if (key[j] == lo && need > 0) {
+                    taken |= (Mask)1 << j;
+                    --need;
+                }
+            }
         }
+        cnt = k;
     }
     // ascending-index output: lanes hold ascending slices; prefix-count the kept entries
     const int mine = MAXPER <= 32 ? __popc((uint32_t)taken) : __popcll((uint64_t)taken);

@@ -78,7 +78,9 @@ def test_mlp_forward_backward_match_oracle(rend, B, refl_len):
     np.testing.assert_array_equal(g2, g.astype(np.float32))
 
 
-@pytest.mark.parametrize("n,refl_len", [(1000, 200), (129, 33), (1, 256), (300, 256)])
+@pytest.mark.parametrize("n,refl_len", [(1000, 200), (129, 33), (1, 256), (300, 256),
+                                        # several 128-row tiles per CTA, ragged last tile
+                                        (2 * 152 * 128 + 3 * 128 + 77, 200), (41000, 33)])
 def test_tensor_core_inference_matches_fp32_forward(rend, n, refl_len):
     """BF16 tensor-core inference against the FP32 kernels (and the FP64 oracle): the
     weights and activations are rounded to BF16 (8-bit significand), so the filters agree to
