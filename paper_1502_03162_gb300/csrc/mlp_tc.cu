@@ -49,7 +49,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&p);
 }
 
-__device__ __forceinline__ float softplus_f(float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); }
+// softplus(z) = max(z, 0) + log(1 + e^-|z|) with the hardware exp2/log2 approximations: an
+// absolute error of a few 1e-7, far below the BF16 rounding of the operands
+__device__ __forceinline__ float softplus_f(float z) { return fmaxf(z, 0.f) + __logf(1.f + __expf(-fabsf(z))); }
 
 __device__ __forceinline__ void tm_ld32(uint32_t taddr, uint32_t (&r)[32])
 {
@@ -112,17 +114,37 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
 
     // ---- A operand of tile t ----
     // layers after the first: step j = row kWarps j + warp, lane = 16-byte chunk (kKc = 32
-    // chunks a row), loaded into registers one tile ahead
+    // chunks a row), loaded into registers two tiles ahead (pre: the next tile, pre2: the one
+    // after), so that two tiles of rows are in flight per SM; the first layer: the direction
+    // row of the next tile (dpre)
     static_assert(kKc == 32 && kRows % kWarps == 0, "one row of chunks per warp and step");
     constexpr int kSteps = kRows / kWarps;
-    uint4 pre[kSteps];
-    auto load_a = [&](int64_t t) {
+    uint4 pre[kSteps], pre2[kSteps];
+    float dpre[3] = {0.f, 0.f, 0.f};
+    auto load_a = [&](int64_t t, uint4 (&dst)[kSteps]) {
 #pragma unroll
         for (int j = 0; j < kSteps; ++j) {
             const int64_t r = t * kRows + kWarps * j + warp;
-            pre[j] = (t < n_tiles && r < a.n_rows) ? __ldg(reinterpret_cast<const uint4 *>(a.in + r * kK) + lane)
+            dst[j] = (t < n_tiles && r < a.n_rows) ? __ldg(reinterpret_cast<const uint4 *>(a.in + r * kK) + lane)
                                                    : make_uint4(0, 0, 0, 0);
         }
+    };
+    auto load_dirs = [&](int64_t t) {
+        const int64_t r = t * kRows + (tid & (kRows - 1));
+        if (t < n_tiles && r < a.n_rows) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) dpre[i] = __ldg(a.dirs + r * 3 + i);
+        }
+    };
+    // the next tile's registers move up: pre <- pre2, and pre2 starts loading tile t
+    auto advance = [&](int64_t t) {
+        if (a.first) {
+            load_dirs(t);
+            return;
+        }
+#pragma unroll
+        for (int j = 0; j < kSteps; ++j) pre[j] = pre2[j];
+        load_a(t, pre2);
     };
     // the first layer: row tid % 128, hidden units [128 h, 128 h + 128) with h = tid / 128:
     // features, then relu(W1 x + b1)
@@ -137,10 +159,9 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
         const int64_t r = t * kRows + row;
         float sa = 0.f, ca = 0.f, se = 0.f, ce = 0.f, ear = 0.f;
         if (r < a.n_rows) {
-            const float *d = a.dirs + r * 3;
-            sincosf(d[0], &sa, &ca);
-            sincosf(d[1], &se, &ce);
-            ear = d[2];
+            __sincosf(dpre[0], &sa, &ca);  // hardware approximations: the features go
+            __sincosf(dpre[1], &se, &ce);  // into BF16 products
+            ear = dpre[2];
         }
         const float x[kMlpIn] = {sa, ca, se, ce, ear};
         for (int kc = h * kKc / 2; kc < (h + 1) * kKc / 2; ++kc) {
@@ -229,10 +250,15 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
     int64_t t = blockIdx.x;
     uint32_t phase = 0, b = 0;
     if (t < n_tiles) {
-        if (!a.first) load_a(t);
+        if (a.first) {
+            load_dirs(t);
+        } else {
+            load_a(t, pre);
+            load_a(t + gridDim.x, pre2);
+        }
         build_a(t);
         issue_mma(0);
-        if (!a.first) load_a(t + gridDim.x);
+        advance(t + (a.first ? 1 : 2) * (int64_t)gridDim.x);
     }
     for (; t < n_tiles; t += gridDim.x) {
         const bool ok = mbar_wait_bounded(smem_addr(bar), phase, abort_flag, a.status);   // MMAs of t
@@ -243,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
         if (tn < n_tiles) {
             build_a(tn);                            // A is free: the MMAs of t completed
             issue_mma(b ^ 1u);
-            if (!a.first) load_a(tn + gridDim.x);   // in flight during the epilogue
+            advance(tn + (a.first ? 1 : 2) * (int64_t)gridDim.x);   // in flight during the epilogue
         }
         epilogue(t, b);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
