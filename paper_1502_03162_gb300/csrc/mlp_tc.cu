@@ -113,20 +113,22 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
     const int64_t n_tiles = (a.n_rows + kRows - 1) / kRows;
 
     // ---- A operand of tile t ----
-    // layers after the first: step j = row kWarps j + warp, lane = 16-byte chunk (kKc = 32
-    // chunks a row), loaded into registers two tiles ahead (pre: the next tile, pre2: the one
-    // after), so that two tiles of rows are in flight per SM; the first layer: the direction
-    // row of the next tile (dpre)
-    static_assert(kKc == 32 && kRows % kWarps == 0, "one row of chunks per warp and step");
-    constexpr int kSteps = kRows / kWarps;
+    // layers after the first: step j of warp w takes rows 8 j + (lane % 8) and 16-byte chunks
+    // 4 w + lane / 8: a load uses whole 32-byte sectors, and each 8-lane phase of the store
+    // fills one 128-byte core matrix (no bank conflicts).  Loaded into registers two tiles
+    // ahead (pre: the next tile, pre2: the one after), so that two tiles of rows are in flight
+    // per SM.  The first layer: the direction row of the next tile (dpre).
+    static_assert(kKc == 4 * kWarps && kRows == 8 * 16, "8 rows x 4 chunks per warp and step");
+    constexpr int kSteps = kRows / 8;
     uint4 pre[kSteps], pre2[kSteps];
     float dpre[3] = {0.f, 0.f, 0.f};
     auto load_a = [&](int64_t t, uint4 (&dst)[kSteps]) {
 #pragma unroll
         for (int j = 0; j < kSteps; ++j) {
-            const int64_t r = t * kRows + kWarps * j + warp;
-            dst[j] = (t < n_tiles && r < a.n_rows) ? __ldg(reinterpret_cast<const uint4 *>(a.in + r * kK) + lane)
-                                                   : make_uint4(0, 0, 0, 0);
+            const int64_t r = t * kRows + 8 * j + (lane & 7);
+            dst[j] = (t < n_tiles && r < a.n_rows)
+                         ? __ldg(reinterpret_cast<const uint4 *>(a.in + r * kK) + 4 * warp + (lane >> 3))
+                         : make_uint4(0, 0, 0, 0);
         }
     };
     auto load_dirs = [&](int64_t t) {
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
         if (!a.first) {
 #pragma unroll
             for (int j = 0; j < kSteps; ++j)
-                *reinterpret_cast<uint4 *>(Am + core_off(kWarps * j + warp, lane * 8)) = pre[j];
+                *reinterpret_cast<uint4 *>(Am + core_off(8 * j + (lane & 7), (4 * warp + (lane >> 3)) * 8)) = pre[j];
             return;
         }
         const int row = tid & (kRows - 1), h = tid / kRows;
