@@ -145,8 +145,11 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
 
 /* Same as hrir_render_batch with HOST buffers: src [n_src][src_ld], dir [n_src] and out
  * [2][out_ld] live in CPU memory (page-locked memory gives the fastest copies).  The
- * call copies the sources to the device (pipelined with rendering), renders, copies the
- * mix back and returns when `out` holds the result.  Device staging space comes from the
+ * call copies the sources to the device on a stream of the context, in up to 4 chunks of
+ * sources (16 or more sources; one chunk otherwise); each chunk is rendered on `stream` as
+ * soon as it has landed, while the next ones copy, and the chunk mixes are summed in chunk
+ * order.  The result equals hrir_render_batch's up to the order of the FP32 sums (and is
+ * deterministic); the call returns when `out` holds it.  Device staging space comes from the
  * context workspace. */
 int hrir_render_batch_host(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld,
                            hrir_dtype dt, const void *src, const int32_t *dir, hrir_mode mode,

@@ -278,6 +278,9 @@ void hrir_destroy(hrir_ctx *ctx)
     hrir_stream_close(ctx);
     free_tables(ctx);
     drop_timing_events(ctx);
+    for (cudaEvent_t &e : ctx->copy_ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     cudaFree(ctx->d_partial);
     cudaFree(ctx->d_stage);
     cudaFree(ctx->d_mlp_ws);
@@ -605,26 +608,57 @@ int hrir_render_batch_host(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld
     const int64_t vec = 16 / (int64_t)es;
     const int64_t dld = round_up(std::max<int64_t>(len, 1), vec);
     const size_t src_bytes = (size_t)n_src * dld * es;
+    // The sources go over in up to kHostChunks chunks on the context's copy stream; chunk c is
+    // rendered on the caller's stream as soon as it has landed (while the next chunks copy),
+    // into its own output planes, and the planes are summed in chunk order (the render is
+    // linear in the sources and the resonance follows the mix, Eq. 2).
+    constexpr int kHostChunks = 4;
+    const int n_chunks = n_src >= 4 * kHostChunks ? kHostChunks : 1;
     const size_t dir_off = round_up((int64_t)src_bytes, 256);
     const size_t out_off = round_up((int64_t)(dir_off + (size_t)n_src * 4), 256);
-    const size_t need = out_off + 2 * (size_t)out_len * 4;
+    const size_t plane = 2 * (size_t)out_len * 4;
+    const size_t need = out_off + (size_t)n_chunks * plane;
     int rc = grow(ctx, &ctx->d_stage, &ctx->stage_bytes, need);
     if (rc) return rc;
     unsigned char *base = static_cast<unsigned char *>(ctx->d_stage);
-    void *d_src = base;
     int32_t *d_dir = reinterpret_cast<int32_t *>(base + dir_off);
     float *d_out = reinterpret_cast<float *>(base + out_off);
-    if (n_src > 0) {
-        if (dld == src_ld) {
-            CUDA_TRY(ctx, cudaMemcpyAsync(d_src, src, src_bytes, cudaMemcpyHostToDevice, st));
-        } else {
-            CUDA_TRY(ctx, cudaMemcpy2DAsync(d_src, dld * es, src, src_ld * es, len * es, n_src,
-                                            cudaMemcpyHostToDevice, st));
+    if (n_src == 0) {
+        rc = hrir_render_batch(ctx, 0, len, dld, dt, base, d_dir, mode, full, d_out, out_len, stream);
+        if (rc) return rc;
+    } else {
+        if (!ctx->copy_stream) {
+            CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+            for (cudaEvent_t &e : ctx->copy_ev) CUDA_TRY(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         }
-        CUDA_TRY(ctx, cudaMemcpyAsync(d_dir, dir, (size_t)n_src * 4, cudaMemcpyHostToDevice, st));
+        cudaStream_t cs = ctx->copy_stream;
+        // the staging buffers are free once the caller's earlier work on `stream` is done
+        CUDA_TRY(ctx, cudaEventRecord(ctx->copy_ev[kHostChunks], st));
+        CUDA_TRY(ctx, cudaStreamWaitEvent(cs, ctx->copy_ev[kHostChunks], 0));
+        for (int c = 0; c < n_chunks; ++c) {
+            const int64_t s0 = (int64_t)n_src * c / n_chunks, s1 = (int64_t)n_src * (c + 1) / n_chunks;
+            unsigned char *d_src = base + (size_t)s0 * dld * es;
+            const unsigned char *h_src = static_cast<const unsigned char *>(src) + (size_t)s0 * src_ld * es;
+            if (dld == src_ld) {
+                CUDA_TRY(ctx, cudaMemcpyAsync(d_src, h_src, (size_t)(s1 - s0) * dld * es, cudaMemcpyHostToDevice, cs));
+            } else {
+                CUDA_TRY(ctx, cudaMemcpy2DAsync(d_src, dld * es, h_src, src_ld * es, len * es, (size_t)(s1 - s0),
+                                                cudaMemcpyHostToDevice, cs));
+            }
+            CUDA_TRY(ctx, cudaMemcpyAsync(d_dir + s0, dir + s0, (size_t)(s1 - s0) * 4, cudaMemcpyHostToDevice, cs));
+            CUDA_TRY(ctx, cudaEventRecord(ctx->copy_ev[c], cs));
+        }
+        for (int c = 0; c < n_chunks; ++c) {
+            const int64_t s0 = (int64_t)n_src * c / n_chunks, s1 = (int64_t)n_src * (c + 1) / n_chunks;
+            CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->copy_ev[c], 0));
+            rc = hrir_render_batch(ctx, (int)(s1 - s0), len, dld, dt, base + (size_t)s0 * dld * es, d_dir + s0,
+                                   mode, full, reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(d_out) + c * plane),
+                                   out_len, stream);
+            if (rc) return rc;
+        }
+        // the chunk planes summed in chunk order, in place over the first
+        if (n_chunks > 1) CUDA_TRY(ctx, launch_add_parts(d_out, out_len, d_out, n_chunks, out_len, st));
     }
-    rc = hrir_render_batch(ctx, n_src, len, dld, dt, d_src, d_dir, mode, full, d_out, out_len, stream);
-    if (rc) return rc;
     CUDA_TRY(ctx, cudaMemcpy2DAsync(out, out_ld * 4, d_out, out_len * 4, out_len * 4, 2,
                                     cudaMemcpyDeviceToHost, st));
     return hrir_sync(ctx, stream);

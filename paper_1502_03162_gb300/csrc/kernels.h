@@ -91,6 +91,9 @@ struct ReduceArgs {
     int64_t out_ld;
 };
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
+// out[e][0, n) (row stride out_ld) = sum over c of parts[c][e][0, n), in c order
+cudaError_t launch_add_parts(float *out, int64_t out_ld, const float *parts, int n_parts, int64_t n,
+                             cudaStream_t st);
 
 // ---- overlap-save FFT convolution with frequency-domain mixing -------------------------
 constexpr int kFftSize = 4096;                    // frame P

@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArg
             const int n = mcnt[jc * 2 + e];
             uint64_t cur[2] = {0, 0}, prv[2] = {0, 0};   // outputs (0, 1), (2, 3)
             if (fade) {
-#pragma unroll 2
+#pragma unroll 4
                 for (int i = 0; i < n; ++i) {
                     const int4 tp = m[i];
                     const float4 v = *reinterpret_cast<const float4 *>(yl + tp.x);
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, 3) moving_mix_kernel(const MovingArg
                     fma2(cur[1], wc, v.z, v.w);
                 }
             } else {
-#pragma unroll 2
+#pragma unroll 4
                 for (int i = 0; i < n; ++i) {
                     const int4 tp = m[i];
                     if (tp.z == 0) continue;              // a tap of the previous filter only

@@ -60,7 +60,28 @@ __global__ void __launch_bounds__(kThreads) reduce_fir_kernel(const ReduceArgs a
     }
 }
 
+// out[e][n] = sum_c parts[c][e][n] in c order (2 planes of n floats per part).
+__global__ void add_parts_kernel(float *__restrict__ out, int64_t out_ld, const float *__restrict__ parts,
+                                 int n_parts, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n; i += (int64_t)gridDim.x * blockDim.x) {
+        float acc = parts[i];
+        for (int c = 1; c < n_parts; ++c) acc += parts[(size_t)c * 2 * n + i];
+        const int64_t e = i / n;
+        out[e * out_ld + (i - e * n)] = acc;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_add_parts(float *out, int64_t out_ld, const float *parts, int n_parts, int64_t n,
+                             cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = (2 * n + 255) / 256;
+    add_parts_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(out, out_ld, parts, n_parts, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st)
 {
