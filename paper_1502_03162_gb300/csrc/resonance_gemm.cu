@@ -154,20 +154,30 @@ __global__ void __launch_bounds__(kThreads) resonance_gemm_kernel(const __grid_c
 
     const int n_tiles = (int)((a.out_len + kTileOut - 1) / kTileOut);
     const int64_t units = (int64_t)n_tiles * a.n_src;
+    // ---- stage y[t0 - 256, t0 + 4096) of unit u (hardware zero fill outside [0, len)); the
+    // window is staged for the next unit as soon as A has been built from it, so the load
+    // overlaps this unit's MMAs and epilogue ----
+    auto stage = [&](int64_t u) {
+        if (warp != 0) return;
+        const int s = (int)(u / n_tiles);
+        const int64_t t0 = (u - (int64_t)s * n_tiles) * kTileOut;
+        if (lane == 0) mbar_arrive_expect_tx(smem_addr(&bars[0]), kWin * (uint32_t)sizeof(T));
+        __syncwarp();
+        for (int b = lane; b < kWin / kBox; b += 32)
+            tma_load_2d(smem_addr(yw + b * kBox), &tmap, (int)(t0 - kBox + b * kBox), s, smem_addr(&bars[0]));
+    };
     uint32_t phase = 0;
+    bool in_flight = false;                 // a staged window not yet waited for
+    if ((int64_t)blockIdx.x < units) {
+        stage(blockIdx.x);
+        in_flight = true;
+    }
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
         const int s = (int)(u / n_tiles);
         const int t = (int)(u - (int64_t)s * n_tiles);
         const int64_t t0 = (int64_t)t * kTileOut;
-        // ---- stage y[t0 - 256, t0 + 4096) (hardware zero fill outside [0, len)) ----
-        if (warp == 0) {
-            if (lane == 0) mbar_arrive_expect_tx(smem_addr(&bars[0]), kWin * (uint32_t)sizeof(T));
-            __syncwarp();
-            for (int b = lane; b < kWin / kBox; b += 32)
-                tma_load_2d(smem_addr(yw + b * kBox), &tmap, (int)(t0 - kBox + b * kBox), s,
-                            smem_addr(&bars[0]));
-        }
         bool ok = mbar_wait_bounded(smem_addr(&bars[0]), phase, abort_flag, a.status);
+        if (ok) in_flight = false;
         // ---- A[b][m] = y[t0 + 32 b + m - 32] = yw[256 + 32 b + m - 32] ----
         if (ok) {
             for (int i = tid; i < kRows * kKA / 8; i += kThreads) {
@@ -181,6 +191,11 @@ __global__ void __launch_bounds__(kThreads) resonance_gemm_kernel(const __grid_c
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (*abort_flag) break;
+        // every thread has read the window: stage the next unit's
+        if (u + gridDim.x < units) {
+            stage(u + gridDim.x);
+            in_flight = true;
+        }
         // ---- D[128][64] = sum over 12 K-steps (A's 4 steps, repeated per term) ----
         if (tid == 0) {
 #pragma unroll 1
@@ -201,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) resonance_gemm_kernel(const __grid_c
         }
         ok = mbar_wait_bounded(smem_addr(&bars[1]), phase, abort_flag, a.status);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        phase ^= 1;
+        phase ^= 1;                          // both barriers complete once per unit
         // ---- epilogue: TMEM lane = output block, 32 columns per ear.  A warp's 32 blocks
         // are 1024 consecutive outputs, so each ear goes through the (now free) A tile in shared
         // memory -- row = block, 16-byte chunk j of row L stored at chunk j ^ (L & 7), so that
@@ -243,10 +258,10 @@ __global__ void __launch_bounds__(kThreads) resonance_gemm_kernel(const __grid_c
         if (!ok) break;
     }
     if (warp == 0) {
-        // a staged load still in flight after an abort lands before the CTA exits (bounded)
+        // a staged load still in flight after an abort lands before the CTA exits (bounded):
+        // its phase is the one after the last completed window
         const uint64_t t0 = global_timer_ns();
-        while (!mbar_try_wait(smem_addr(&bars[0]), phase) && *abort_flag &&
-               global_timer_ns() - t0 < kWaitLimitNs) {
+        while (in_flight && !mbar_try_wait(smem_addr(&bars[0]), phase) && global_timer_ns() - t0 < kWaitLimitNs) {
         }
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                      : "memory");
