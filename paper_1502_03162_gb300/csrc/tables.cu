@@ -64,6 +64,22 @@ __device__ __forceinline__ void topk_row(const float (&v)[MAXPER], int row, int 
         cnt = total;
     } else {
         uint32_t lo = 1, hi = __reduce_max_sync(0xffffffffu, kmax) + 1u;   // #(>= lo) >= k > #(>= hi)
+        if (k <= 32) {
+            // a tighter start: the k-th largest lane maximum (k lanes hold a key at least that
+            // large), from a bitonic sort of the 32 lane maxima (ascending across the lanes)
+            uint32_t x = kmax;
+#pragma unroll
+            for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, stride);
+                    const bool asc = (lane & size) == 0, lower = (lane & stride) == 0;
+                    x = (asc == lower) ? (x < y ? x : y) : (x > y ? x : y);
+                }
+            }
+            const uint32_t kth = __shfl_sync(0xffffffffu, x, 32 - k);
+            lo = kth > 1u ? kth : 1u;
+        }
         bool exact = false;
         while (hi - lo > 1u) {
             const uint32_t mid = lo + (hi - lo) / 2u;
