@@ -368,6 +368,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="only the headline sparse K=16 path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", action="store_true", help="skip the serving-loop benchmark")
+    ap.add_argument("--learned-sources", type=int, default=4096,
+                    help="moving sources of the learned-filter workload (smaller for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -512,7 +514,7 @@ def main():
     if not args.no_extras:
         load(K_DEFAULT)
         result["precision"] = bench_precision(rend, torch, src, dirs, L, max(3, args.steps // 5))
-        result["learned"] = bench_learned(rend, torch)
+        result["learned"] = bench_learned(rend, torch, S=args.learned_sources)
 
     if not args.no_stream:
         load(K_DEFAULT)
