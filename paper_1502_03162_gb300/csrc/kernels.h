@@ -179,15 +179,16 @@ struct MlpTcArgs {
     const float *dirs;           // [n_rows][3] (first layer only)
     const float *W1, *b1;        // first layer only
     int first, last;
-    const __nv_bfloat16 *in;     // [n_rows][256] (not first)
+    const __nv_bfloat16 *in;     // (not first) tiles of 128 rows x 256, canonical operand layout
     const float *W;              // [N][256] FP32 (converted to BF16 in shared memory)
     const float *b;              // [N]
     int N, n_pad;                // N <= n_pad <= 256, n_pad % 16 == 0
-    __nv_bfloat16 *hout;         // [n_rows][256] (not last)
+    __nv_bfloat16 *hout;         // (not last) ceil(n_rows / 128) tiles of 128 x 256, same layout
     float *out;                  // [n_rows][N] (last)
+    int stage_out;               // (set by the launcher) output rows staged for coalesced stores
     int *status;
 };
-size_t mlp_tc_smem_bytes(int n_pad);
+size_t mlp_tc_smem_bytes(int n_pad, int stage_out);
 cudaError_t launch_mlp_layer_tc(const MlpTcArgs &a, int grid, cudaStream_t st);
 
 // ---- moving sources: per-segment filters with a linear crossfade ---------------------------

@@ -150,10 +150,12 @@ int hrir_mlp_forward_bf16(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int 
     cudaStream_t st = (cudaStream_t)stream;
     const MlpLayout L(refl_len);
     const int64_t chunk = std::min<int64_t>(n_rows, kTcChunk);
-    int rc = grow_ws(ctx, (size_t)chunk * H * 2 * sizeof(__nv_bfloat16));
+    // hidden activations in whole 128-row tiles (the tensor-core operand layout)
+    const int64_t chunk_rows = round_up(chunk, 128);
+    int rc = grow_ws(ctx, (size_t)chunk_rows * H * 2 * sizeof(__nv_bfloat16));
     if (rc) return rc;
     __nv_bfloat16 *h1 = static_cast<__nv_bfloat16 *>(ctx->d_mlp_ws);
-    __nv_bfloat16 *h2 = h1 + (size_t)chunk * H;
+    __nv_bfloat16 *h2 = h1 + (size_t)chunk_rows * H;
     KernelTimer kt(ctx, HRIR_K_MLP, st);
     for (int64_t r0 = 0; r0 < n_rows; r0 += chunk) {
         const int64_t nb = std::min(chunk, n_rows - r0);

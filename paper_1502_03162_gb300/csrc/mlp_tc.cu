@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
     int *abort_flag = reinterpret_cast<int *>(bar + 1) + 1;
     float *bias = reinterpret_cast<float *>(bar + 2);                    // [256] this layer's biases
     float *w1 = bias + kK;                                               // layer 2: W1 [256][5], b1 [256]
+    float *stage_out = w1 + kMlpHidden * (kMlpIn + 1);                   // output layer: [8 warps][32][32]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -113,23 +114,22 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
     const int64_t n_tiles = (a.n_rows + kRows - 1) / kRows;
 
     // ---- A operand of tile t ----
-    // layers after the first: step j of warp w takes rows 8 j + (lane % 8) and 16-byte chunks
-    // 4 w + lane / 8: a load uses whole 32-byte sectors, and each 8-lane phase of the store
-    // fills one 128-byte core matrix (no bank conflicts).  Loaded into registers two tiles
-    // ahead (pre: the next tile, pre2: the one after), so that two tiles of rows are in flight
-    // per SM.  The first layer: the direction row of the next tile (dpre).
-    static_assert(kKc == 4 * kWarps && kRows == 8 * 16, "8 rows x 4 chunks per warp and step");
-    constexpr int kSteps = kRows / 8;
+    // layers after the first: the hidden activations are kept in HBM tile by tile in the
+    // operand's own canonical layout (128 rows x 256 columns of BF16 = 64 KB a tile, element
+    // (row, k) at core_off(row, k)), so tile t is one contiguous block: step j moves 16-byte
+    // chunk j kThreads + tid of it (coalesced loads, conflict-free stores).  Loaded into
+    // registers two tiles ahead (pre: the next tile, pre2: the one after), so that two tiles
+    // are in flight per SM.  The first layer: the direction row of the next tile (dpre).
+    constexpr int kTileChunks = kRows * kK / 8;
+    static_assert(kTileChunks % kThreads == 0, "whole steps");
+    constexpr int kSteps = kTileChunks / kThreads;
     uint4 pre[kSteps], pre2[kSteps];
     float dpre[3] = {0.f, 0.f, 0.f};
     auto load_a = [&](int64_t t, uint4 (&dst)[kSteps]) {
+        const uint4 *blk = reinterpret_cast<const uint4 *>(a.in) + t * kTileChunks;
 #pragma unroll
-        for (int j = 0; j < kSteps; ++j) {
-            const int64_t r = t * kRows + 8 * j + (lane & 7);
-            dst[j] = (t < n_tiles && r < a.n_rows)
-                         ? __ldg(reinterpret_cast<const uint4 *>(a.in + r * kK) + 4 * warp + (lane >> 3))
-                         : make_uint4(0, 0, 0, 0);
-        }
+        for (int j = 0; j < kSteps; ++j)
+            dst[j] = t < n_tiles ? __ldg(blk + j * kThreads + tid) : make_uint4(0, 0, 0, 0);
     };
     auto load_dirs = [&](int64_t t) {
         const int64_t r = t * kRows + (tid & (kRows - 1));
@@ -153,8 +153,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
     auto build_a = [&](int64_t t) {
         if (!a.first) {
 #pragma unroll
-            for (int j = 0; j < kSteps; ++j)
-                *reinterpret_cast<uint4 *>(Am + core_off(8 * j + (lane & 7), (4 * warp + (lane >> 3)) * 8)) = pre[j];
+            for (int j = 0; j < kSteps; ++j) reinterpret_cast<uint4 *>(Am)[j * kThreads + tid] = pre[j];
             return;
         }
         const int row = tid & (kRows - 1), h = tid / kRows;
@@ -210,6 +209,9 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
     };
     // epilogue of tile t from accumulator buffer b: warp (lane quarter warp % 4) takes the
     // 32-column chunks c of parity warp / 4
+    // output layer with rows of 16-byte groups at a 16-byte aligned base and room for the
+    // staging tiles (set by the launcher): staged, coalesced stores
+    const bool vec_out = a.stage_out != 0;
     auto epilogue = [&](int64_t t, uint32_t b) {
         const int q = warp & 3, half = warp >> 2;
         const int row = q * 32 + lane;
@@ -217,6 +219,30 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
         for (int c0 = 32 * half; c0 < a.n_pad; c0 += 64) {
             uint32_t v[32];
             tm_ld32(tmem + b * 256u + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+            if (a.last && vec_out) {
+                // the warp's 32 rows x 32 columns through shared memory (16-byte chunk j of row
+                // L at chunk j ^ (L % 8): conflict-free both ways), then 4 whole 128-byte rows
+                // per store instruction
+                float *stg = stage_out + warp * 32 * 32;
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    reinterpret_cast<float4 *>(stg + lane * 32)[j ^ (lane & 7)] = make_float4(
+                        softplus_f(__uint_as_float(v[4 * j]) + bias[c0 + 4 * j]),
+                        softplus_f(__uint_as_float(v[4 * j + 1]) + bias[c0 + 4 * j + 1]),
+                        softplus_f(__uint_as_float(v[4 * j + 2]) + bias[c0 + 4 * j + 2]),
+                        softplus_f(__uint_as_float(v[4 * j + 3]) + bias[c0 + 4 * j + 3]));
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int rr = 4 * i + (lane >> 3), c = lane & 7;
+                    const float4 x = reinterpret_cast<const float4 *>(stg + rr * 32)[c ^ (rr & 7)];
+                    const int64_t ro = t * kRows + q * 32 + rr;
+                    if (ro < a.n_rows && c0 + 4 * c < a.N)
+                        *reinterpret_cast<float4 *>(a.out + ro * a.N + c0 + 4 * c) = x;
+                }
+                __syncwarp();
+                continue;
+            }
             if (r >= a.n_rows) continue;
             if (a.last) {
                 float *o = a.out + r * a.N;
@@ -240,9 +266,13 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
                 for (int j = 0; j < 32; j += 2)
                     hv[j / 2] = pack_bf16(fmaxf(__uint_as_float(v[j]) + bias[c0 + j], 0.f),
                                           fmaxf(__uint_as_float(v[j + 1]) + bias[c0 + j + 1], 0.f));
-                uint4 *o = reinterpret_cast<uint4 *>(a.hout + r * kK + c0);
+                // the tile's block in the canonical layout: a warp's 32 rows x 16 bytes are four
+                // whole 128-byte core matrices
+                __nv_bfloat16 *blk = a.hout + t * (int64_t)(kRows * kK);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) o[j] = make_uint4(hv[4 * j], hv[4 * j + 1], hv[4 * j + 2], hv[4 * j + 3]);
+                for (int j = 0; j < 4; ++j)
+                    *reinterpret_cast<uint4 *>(blk + core_off(row, c0 + 8 * j)) =
+                        make_uint4(hv[4 * j], hv[4 * j + 1], hv[4 * j + 2], hv[4 * j + 3]);
             }
         }
     };
@@ -295,19 +325,23 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_layer_tc_kernel(const MlpTcAr
 
 }  // namespace
 
-size_t mlp_tc_smem_bytes(int n_pad)
+size_t mlp_tc_smem_bytes(int n_pad, int stage_out)
 {
-    return (size_t)(n_pad + kRows) * kK * 2 + 16 + (size_t)kK * 4 + (size_t)kMlpHidden * (kMlpIn + 1) * 4;
+    return (size_t)(n_pad + kRows) * kK * 2 + 16 + (size_t)kK * 4 + (size_t)kMlpHidden * (kMlpIn + 1) * 4 +
+           (stage_out ? (size_t)kWarps * 32 * 32 * 4 : 0);
 }
 
 cudaError_t launch_mlp_layer_tc(const MlpTcArgs &a, int grid, cudaStream_t st)
 {
     if (a.n_pad < 16 || a.n_pad > 256 || a.n_pad % 16 || a.N > a.n_pad) return cudaErrorInvalidValue;
-    const size_t smem = mlp_tc_smem_bytes(a.n_pad);
+    MlpTcArgs b = a;
+    b.stage_out = a.last && (a.N & 3) == 0 && ((uintptr_t)a.out & 15) == 0 &&
+                  mlp_tc_smem_bytes(a.n_pad, 1) <= 227 * 1024;
+    const size_t smem = mlp_tc_smem_bytes(a.n_pad, b.stage_out);
     cudaError_t e = cudaFuncSetAttribute(mlp_layer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    mlp_layer_tc_kernel<<<grid, kThreads, smem, st>>>(a);
+    mlp_layer_tc_kernel<<<grid, kThreads, smem, st>>>(b);
     return cudaGetLastError();
 }
 
