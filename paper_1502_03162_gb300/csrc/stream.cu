@@ -206,7 +206,9 @@ struct hrir_stream {
     StepSlot *h_slots = nullptr;
     float *h_out = nullptr;
     std::vector<int64_t> row_sessions;
-    std::vector<int> step_slot_ids;
+    std::vector<int> order;                   // used slots in (session, slot) order
+    std::vector<int> pending;                 // admitted since the last step (upload in flight)
+    int *h_status = nullptr;                  // status word after each step (page-locked)
     cudaGraphExec_t graph = nullptr;
     cudaGraph_t graph_def = nullptr;
 };
@@ -228,6 +230,7 @@ void stream_free(hrir_stream *s)
     cudaFreeHost(s->h_rows);
     cudaFreeHost(s->h_slots);
     cudaFreeHost(s->h_out);
+    cudaFreeHost(s->h_status);
     if (s->copy_st) cudaStreamDestroy(s->copy_st);
     delete s;
 }
@@ -274,6 +277,7 @@ int hrir_stream_open(hrir_ctx *ctx, int block, int max_slots, size_t pool_bytes,
         if ((e = cudaHostAlloc(&s->h_out, (size_t)max_slots * 2 * block * sizeof(float), cudaHostAllocMapped)) !=
             cudaSuccess)
             break;
+        if ((e = cudaHostAlloc(&s->h_status, sizeof(int), cudaHostAllocDefault)) != cudaSuccess) break;
     } while (0);
     if (e != cudaSuccess) {
         stream_free(s);
@@ -289,7 +293,8 @@ int hrir_stream_open(hrir_ctx *ctx, int block, int max_slots, size_t pool_bytes,
     }
     s->h_hdr->n_rows = 0;
 
-    // Capture the step: one kernel node with device views of the mapped descriptor/output.
+    // Capture the step: one kernel node with device views of the mapped descriptor/output,
+    // then the status word copied to page-locked host memory (read after the step's sync).
     StreamArgs a;
     void *p = nullptr;
     cudaHostGetDevicePointer(&p, s->h_hdr, 0);
@@ -317,6 +322,13 @@ int hrir_stream_open(hrir_ctx *ctx, int block, int max_slots, size_t pool_bytes,
         if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) break;
         if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
         stream_step_kernel<<<grid, 256, 0, cap>>>(a);
+        if ((e = cudaMemcpyAsync(s->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, cap)) !=
+            cudaSuccess) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(cap, &g);
+            if (g) cudaGraphDestroy(g);
+            break;
+        }
         if ((e = cudaStreamEndCapture(cap, &s->graph_def)) != cudaSuccess) break;
         e = cudaGraphInstantiate(&s->graph, s->graph_def, 0);
     } while (0);
@@ -377,6 +389,12 @@ int hrir_stream_admit(hrir_ctx *ctx, int64_t req_id, int64_t session, const floa
         sit = s->sessions.emplace(session, ss).first;
     }
     sit->second.live_slots += 1;
+    // keep the step order (session, slot): insert the new slot at its place
+    const auto before = [&](int x, int y) {
+        return s->slots[x].session != s->slots[y].session ? s->slots[x].session < s->slots[y].session : x < y;
+    };
+    s->order.insert(std::lower_bound(s->order.begin(), s->order.end(), id, before), id);
+    s->pending.push_back(id);
     return HRIR_OK;
 }
 
@@ -392,31 +410,25 @@ int hrir_stream_step(hrir_ctx *ctx, const float **out_blocks, const int64_t **ou
     const int64_t tail = ctx->hrir_len - 1;
     // sources admitted since the last step join this one; the step's kernel waits on the GPU
     // for their uploads (the host does not block)
-    for (auto &sl : s->slots) {
-        if (sl.used && !sl.ready) {
-            HRIR_CUDA_TRY(ctx, cudaStreamWaitEvent(s->st, sl.uploaded, 0));
-            sl.ready = true;
-        }
+    for (int id : s->pending) {
+        HRIR_CUDA_TRY(ctx, cudaStreamWaitEvent(s->st, s->slots[id].uploaded, 0));
+        s->slots[id].ready = true;
     }
-    // descriptor: sessions in id order, each session's ready sources in slot order
+    s->pending.clear();
+    // descriptor: sessions in id order, each session's sources in slot order (the order kept
+    // by hrir_stream_admit)
     s->row_sessions.clear();
-    s->step_slot_ids.clear();
-    for (int i = 0; i < s->max_slots; ++i)
-        if (s->slots[i].used && s->slots[i].ready) s->step_slot_ids.push_back(i);
-    std::stable_sort(s->step_slot_ids.begin(), s->step_slot_ids.end(), [&](int x, int y) {
-        return s->slots[x].session < s->slots[y].session;
-    });
     int n_rows = 0;
-    const int n_sl = (int)s->step_slot_ids.size();
+    const int n_sl = (int)s->order.size();
     for (int j = 0; j < n_sl; ++j) {
-        const Slot &sl = s->slots[s->step_slot_ids[j]];
+        const Slot &sl = s->slots[s->order[j]];
         StepSlot &d = s->h_slots[j];
         d.pool_off = sl.pool_off;
         d.len = sl.len;
         d.pos = sl.pos;
         d.dir = sl.dir;
         d.pad = 0;
-        if (j == 0 || s->slots[s->step_slot_ids[j - 1]].session != sl.session) {
+        if (j == 0 || s->slots[s->order[j - 1]].session != sl.session) {
             Session &ss = s->sessions[sl.session];
             StepRow &r = s->h_rows[n_rows++];
             r.slot_begin = j;
@@ -435,7 +447,9 @@ int hrir_stream_step(hrir_ctx *ctx, const float **out_blocks, const int64_t **ou
     }
     // advance; retire sources whose tails are out, and sessions without sources
     int nd = 0;
-    for (int i : s->step_slot_ids) {
+    size_t kept = 0;
+    for (size_t j = 0; j < s->order.size(); ++j) {
+        const int i = s->order[j];
         Slot &sl = s->slots[i];
         sl.pos += s->block;
         if (sl.pos >= sl.len + tail) {
@@ -449,15 +463,17 @@ int hrir_stream_step(hrir_ctx *ctx, const float **out_blocks, const int64_t **ou
                 s->free_states.push_back(it->second.state);
                 s->sessions.erase(it);
             }
+        } else {
+            s->order[kept++] = i;
         }
     }
+    s->order.resize(kept);
     *out_blocks = s->h_out;
     *out_sessions = s->row_sessions.data();
     *n_out = n_rows;
     *n_done = nd;
-    int st = 0;
     if (n_rows > 0) {
-        HRIR_CUDA_TRY(ctx, cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+        const int st = *s->h_status;          // copied by the step's graph
         if (st) {
             HRIR_CUDA_TRY(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
             return fail(ctx, HRIR_EINVAL, "a direction id was out of range (rendered as silence)");

@@ -277,7 +277,8 @@ class _StepBuffers:
 
 def hrir_stream_step(ctx, bufs: "_StepBuffers", block: int):
     """One step.  Returns (blocks, sessions, done): blocks is a float32 view [n][2][block] of
-    the library's output buffer (valid until the next step), sessions and done are lists."""
+    the library's output buffer (valid until the next step), sessions an int64 array [n] (the
+    session of each block row), done a list of the finished request ids."""
     lib = load_library()
     rc = lib.hrir_stream_step(ctx, ctypes.byref(bufs.out), ctypes.byref(bufs.sess),
                               ctypes.byref(bufs.n_out), bufs.done, ctypes.byref(bufs.n_done))
@@ -285,9 +286,9 @@ def hrir_stream_step(ctx, bufs: "_StepBuffers", block: int):
     n = bufs.n_out.value
     if n:
         blocks = np.ctypeslib.as_array(bufs.out, shape=(n, 2, block))
-        sessions = np.ctypeslib.as_array(bufs.sess, shape=(n,)).tolist()
+        sessions = np.ctypeslib.as_array(bufs.sess, shape=(n,)).copy()
     else:
-        blocks, sessions = np.zeros((0, 2, block), np.float32), []
+        blocks, sessions = np.zeros((0, 2, block), np.float32), np.zeros(0, np.int64)
     return blocks, sessions, list(bufs.done[:bufs.n_done.value])
 
 
