@@ -112,6 +112,26 @@ def test_batched_matches_oracle(rend, S, L, k, n_dirs):
         assert_close(outs[(m, False)], ref[:, :L], what=f"{m} same S={S} L={L}")
 
 
+@pytest.mark.parametrize("refl_len,k", [(300, 16), (700, 24)])
+def test_long_reflection_filters_match_oracle(rend, refl_len, k):
+    """Lg longer than one window segment of 204 filter offsets: the sparse kernel walks
+    ceil(Lg / 204) segments per unit (a window per segment, taps split by segment)."""
+    rng = np.random.default_rng(refl_len + k)
+    n_dirs, S, L = 9, 11, 7001
+    _, idx, w, nnz, res = tables(rng, n_dirs, k, refl_len=refl_len)
+    ld = (L + 7) // 8 * 8 + 8
+    y = np.full((S, ld), np.nan, dtype=np.float32)       # padding must never be read
+    y[:, :L] = synth.sources_ar1(rng, S, L)
+    dirs = synth.directions(rng, S, n_dirs)
+    ref = oracle.render_sparse(y, dirs, idx, w, nnz, refl_len, res, length=L)
+    outs = _render_both(rend, y, dirs, idx, w, nnz, res, length=L, refl_len=refl_len)
+    H = 32 + refl_len - 1
+    for m in MODES:
+        assert outs[(m, True)].shape == (2, L + H - 1)
+        assert_close(outs[(m, True)], ref, what=f"{m} Lg={refl_len}")
+        assert_close(outs[(m, False)], ref[:, :L], what=f"{m} same Lg={refl_len}")
+
+
 def test_edge_cases(rend):
     rng = np.random.default_rng(5)
     _, idx, w, nnz, res = tables(rng, 4, 16)
