@@ -85,6 +85,13 @@ const char *hrir_last_error(const hrir_ctx *ctx);
  * HRIR_ECUDA if the stream reported a CUDA error. */
 int hrir_sync(hrir_ctx *ctx, void *stream);
 
+/* Self-test of the failure path: enqueues on `stream` one thread that waits on a device
+ * barrier nothing ever completes, through the same bounded wait the pipelined kernels use.
+ * After the wait limit (1 s) it sets the context's timeout flag and returns, so the next
+ * hrir_sync(ctx, stream) returns HRIR_ETIMEDOUT (and clears the flag); the context stays
+ * usable.  Returns HRIR_OK once enqueued. */
+int hrir_selftest_wait_timeout(hrir_ctx *ctx, void *stream);
+
 /* ---------------------------------------------------------------------------------------
  * Filter pack: top-K sparsification of non-negative reflection rows (a device kernel).
  * Follows the NNZE budget of Sec. III-D: from each row of g keep the K largest strictly

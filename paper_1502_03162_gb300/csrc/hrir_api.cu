@@ -341,6 +341,14 @@ int hrir_sync(hrir_ctx *ctx, void *stream)
     return fail(ctx, HRIR_EINVAL, "a direction id was out of range (rendered as silence)");
 }
 
+int hrir_selftest_wait_timeout(hrir_ctx *ctx, void *stream)
+{
+    if (!ctx) return fail(nullptr, HRIR_EINVAL, "ctx is NULL");
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    CUDA_TRY(ctx, launch_wait_timeout_selftest(ctx->d_status, (cudaStream_t)stream));
+    return HRIR_OK;
+}
+
 int hrir_topk_pack(hrir_ctx *ctx, int n_rows, int refl_len, int k, const float *g, uint16_t *idx,
                    float *w, uint8_t *nnz, void *stream)
 {

@@ -91,6 +91,8 @@ struct ReduceArgs {
     int64_t out_ld;
 };
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
+// a bounded wait that expires (DEV_TIMEOUT into *status after the wait limit): self-test
+cudaError_t launch_wait_timeout_selftest(int *status, cudaStream_t st);
 // out[e][0, n) (row stride out_ld) = sum over c of parts[c][e][0, n), in c order
 cudaError_t launch_add_parts(float *out, int64_t out_ld, const float *parts, int n_parts, int64_t n,
                              cudaStream_t st);

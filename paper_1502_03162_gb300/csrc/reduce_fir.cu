@@ -72,7 +72,26 @@ __global__ void add_parts_kernel(float *__restrict__ out, int64_t out_ld, const 
     }
 }
 
+// One thread waits on an mbarrier that nothing arrives on, through the bounded wait every
+// pipelined kernel uses: after the wait limit it raises the abort flag and ORs DEV_TIMEOUT
+// into *status, then returns (a self-test of the failure path; nothing hangs or traps).
+__global__ void wait_timeout_selftest_kernel(int *status)
+{
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    mbar_init(smem_addr(&bar), 1);
+    abort_flag = 0;
+    mbar_fence_init();
+    mbar_wait_bounded(smem_addr(&bar), 0u, &abort_flag, status);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_timeout_selftest(int *status, cudaStream_t st)
+{
+    wait_timeout_selftest_kernel<<<1, 1, 0, st>>>(status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_add_parts(float *out, int64_t out_ld, const float *parts, int n_parts, int64_t n,
                              cudaStream_t st)

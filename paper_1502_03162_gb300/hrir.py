@@ -35,6 +35,7 @@ SIGNATURES = {
     "hrir_destroy": ([_vp], None),
     "hrir_last_error": ([_vp], _cp),
     "hrir_sync": ([_vp, _vp], _i),
+    "hrir_selftest_wait_timeout": ([_vp, _vp], _i),
     "hrir_topk_pack": ([_vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "hrir_load_filters": ([_vp, _i, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _i], _i),
     "hrir_out_len": ([_vp, _i64, _i], _i64),
@@ -138,6 +139,12 @@ def hrir_last_error(ctx) -> str:
 def hrir_sync(ctx, stream=None) -> int:
     """Returns the status (does not raise) so callers can test device-side flags."""
     return load_library().hrir_sync(ctx, _stream_handle(stream))
+
+
+def hrir_selftest_wait_timeout(ctx, stream=None) -> int:
+    """Enqueue the failure-path self-test (a bounded device wait that expires after 1 s); the
+    next hrir_sync returns HRIR_ETIMEDOUT."""
+    return load_library().hrir_selftest_wait_timeout(ctx, _stream_handle(stream))
 
 
 def hrir_topk_pack(ctx, g, k: int, idx=None, w=None, nnz=None, stream=None):

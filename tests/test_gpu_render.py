@@ -132,6 +132,20 @@ def test_long_reflection_filters_match_oracle(rend, refl_len, k):
         assert_close(outs[(m, False)], ref[:, :L], what=f"{m} same Lg={refl_len}")
 
 
+def test_expired_wait_reports_timeout_and_context_stays_usable(rend):
+    """The failure path of the bounded device waits: a wait that nothing completes gives up
+    after its limit, the next sync reports HRIR_ETIMEDOUT, and the context still renders."""
+    from paper_1502_03162_gb300 import hrir
+    assert hrir.hrir_selftest_wait_timeout(rend.ctx) == hrir.HRIR_OK
+    assert rend.sync() == hrir.HRIR_ETIMEDOUT
+    assert rend.sync() == 0                               # the flag was cleared
+    cfg = synth.tiny_config(seed=3)
+    idx, w, nnz = oracle.topk(cfg["G"], cfg["k"])
+    ref = oracle.render_sparse(cfg["y"], cfg["dirs"], idx, w, nnz, 200, cfg["res"])
+    outs = _render_both(rend, cfg["y"], cfg["dirs"], idx, w, nnz, cfg["res"], modes=("sparse",))
+    assert_close(outs[("sparse", True)], ref, what="render after an expired wait")
+
+
 def test_edge_cases(rend):
     rng = np.random.default_rng(5)
     _, idx, w, nnz, res = tables(rng, 4, 16)
