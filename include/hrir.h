@@ -243,9 +243,12 @@ int hrir_render_batch_noalloc(hrir_ctx *ctx, int n_src, int64_t len, int64_t src
  * hrir_mlp_forward      out [n_rows][Lg] = g for every row; acts is filled when not NULL
  *                       (otherwise the context workspace holds the activations in chunks).
  * hrir_mlp_forward_bf16 the same filters for inference on the tensor cores: weights and
- *                       activations rounded to BF16, FP32 accumulation, FP32 output
- *                       (Lg <= 256; no activations kept).  For the millions of rows of moving
- *                       sources; agrees with hrir_mlp_forward to BF16 precision.
+ *                       activations rounded to BF16, FP32 accumulation, FP32 output; the
+ *                       features and the softplus use the hardware approximations of sin,
+ *                       cos, exp and log (errors far below the BF16 rounding).  Lg <= 256; the
+ *                       hidden activations stay in the context workspace.  For the millions
+ *                       of rows of moving sources; agrees with hrir_mlp_forward to BF16
+ *                       precision.
  * hrir_mlp_backward     grads [param_count] = dL/dparams for the batch whose forward pass left
  *                       `acts` and `out`; target [n_rows][Lg]; loss (device float, may be
  *                       NULL) = L.  1 <= n_rows <= 2^24.  Deterministic (fixed-order sums).
@@ -278,6 +281,8 @@ int hrir_mlp_adam(hrir_ctx *ctx, int64_t n, float *params, const float *grads, f
  *   tap_idx   device uint16 [n_src][n_seg][2][k_max] (indices < Lg, any order),
  *   tap_w     device float  [n_src][n_seg][2][k_max], tap_nnz device uint8 [n_src][n_seg][2]
  *             (the layout hrir_topk_pack writes for rows ordered (source, segment, ear)).
+ *             With k_max % 4 == 0 and 16-byte aligned tap_idx and tap_w the tables are
+ *             staged by bulk copies; any other k_max works, more slowly.
  *             An index >= Lg or a count > k_max is ignored and flags HRIR_EINVAL for
  *             hrir_sync.
  *   seg_len   a multiple of 128;  1 <= k_max <= 255.
