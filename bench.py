@@ -124,6 +124,52 @@ def profiled_traffic(kernel_file, profile_file):
     return float(m_b.group(1)) if cur == m_sha.group(1) else None
 
 
+class Replicas:
+    """One process per GPU (torchrun): RANK / WORLD_SIZE / LOCAL_RANK from the launcher's
+    environment.  Each rank renders its own independent batch (seed offset by the rank), so
+    there is no collective on the data path: a barrier brackets the timed region, the step
+    time is the maximum over ranks, and the whole-job rate counts every rank's units."""
+
+    def __init__(self, backend="nccl", device="cuda"):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.device = device
+        self.dist = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            if backend == "nccl":
+                dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            else:
+                dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max_over_ranks(self, x):
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def seed(self, base):
+        return base + self.rank
+
+    def whole_job(self, units_per_rank, ms_per_step):
+        """Units of all ranks per second, at the slowest rank's step time."""
+        return units_per_rank * self.world / (ms_per_step / 1e3)
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
 def make_inputs(S, L, seed, torch):
     from paper_1502_03162_gb300 import synth
     ld = (L + 7) // 8 * 8
@@ -376,31 +422,16 @@ def main():
         return
 
     import torch
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ranks = Replicas("nccl", device="cuda")
+    rank, world, local = ranks.rank, ranks.world, ranks.local
+    barrier, max_over_ranks = ranks.barrier, ranks.max_over_ranks
 
     from paper_1502_03162_gb300 import hrir
     import __graft_entry__
     __graft_entry__.build()
     S, L = args.sources, args.length
-    cfg, host = make_inputs(S, L, seed=2 + rank, torch=torch)
+    cfg, host = make_inputs(S, L, seed=ranks.seed(2), torch=torch)
     rend = hrir.Renderer(local)
     G = torch.from_numpy(cfg["G"]).cuda()
     src = host.cuda()
@@ -430,7 +461,7 @@ def main():
     assert rend.sync() == 0
     ms = max_over_ranks(ms)
     units = S * L * 2
-    value = units * world / (ms / 1e3)
+    value = ranks.whole_job(units, ms)
 
     # kernel-level roofline of the dominant kernel (the sparse mixing kernel)
     pk, pk_kind = peaks()
@@ -481,17 +512,17 @@ def main():
         t = time_steps(lambda: rend.render(src, dirs, mode="dense", length=L, out=out),
                        max(2, args.steps // 5), 1, torch, barrier)
         t = max_over_ranks(t)
-        extras["dense_k16"] = {"value": units * world / (t / 1e3), "ms_per_step": t}
+        extras["dense_k16"] = {"value": ranks.whole_job(units, t), "ms_per_step": t}
         # overlap-save FFT convolution (plain method 2), same filters, P = 4096
         t = time_steps(lambda: rend.render(src, dirs, mode="fft", length=L, out=out),
                        max(3, args.steps // 5), 2, torch, barrier)
         t = max_over_ranks(t)
-        extras["fft_p4096"] = {"value": units * world / (t / 1e3), "ms_per_step": t}
+        extras["fft_p4096"] = {"value": ranks.whole_job(units, t), "ms_per_step": t}
         for k in (8, 32):
             load(k)
             t = time_steps(step, max(3, args.steps // 2), 2, torch, barrier)
             t = max_over_ranks(t)
-            extras[f"sparse_k{k}"] = {"value": units * world / (t / 1e3), "ms_per_step": t}
+            extras[f"sparse_k{k}"] = {"value": ranks.whole_job(units, t), "ms_per_step": t}
         load(K_DEFAULT)
         extras["sparse_k16"] = {"value": value, "ms_per_step": ms}
         result["paths"] = extras
@@ -507,7 +538,7 @@ def main():
         e2e_step()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     e2e_ms = max_over_ranks(e2e_ms)
-    result["e2e"] = {"value": units * world / (e2e_ms / 1e3), "unit": "source-ear samples/s",
+    result["e2e"] = {"value": ranks.whole_job(units, e2e_ms), "unit": "source-ear samples/s",
                      "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(S * host.shape[1] * 4 + S * 4),
                      "d2h_bytes_per_step": int(2 * (L + 230) * 4)}
 
@@ -526,8 +557,7 @@ def main():
     if rank == 0:
         print(json.dumps(result))
     rend.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 if __name__ == "__main__":
