@@ -53,27 +53,44 @@ def fp32_peak_tflops(sm_mhz):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock/throttle sampling during the timed region.  The sampler is live (its
+    first sample read) before the caller's warm-up; mark() starts the region, and the summary
+    holds the samples taken after it, including one taken at or after the region's end, so a
+    region shorter than the sampling period is still sampled."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, period_ms=200):
         self.gpu = gpu_index
+        self.period_ms = period_ms
         self.proc = None
         self.lines = []
+        self.first = 0
+
+    def _wait_for_sample(self, n, limit_s):
+        t0 = time.monotonic()
+        while len(self.lines) <= n and time.monotonic() - t0 < limit_s and self.proc.poll() is None:
+            time.sleep(0.005)
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
             self.proc = None
+            return self
+        self._wait_for_sample(0, 5.0)
+        self.mark()
         return self
+
+    def mark(self):
+        """The timed region starts: only samples read from now on are summarised."""
+        self.first = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -81,6 +98,8 @@ class ClockSampler:
 
     def __exit__(self, *exc):
         if self.proc:
+            # one sample at or after the end of the region
+            self._wait_for_sample(len(self.lines), 2.0 * self.period_ms / 1e3)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -90,7 +109,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.first:]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -449,14 +468,15 @@ def main():
     step = lambda: rend.render(src, dirs, mode="sparse", length=L, out=out)  # noqa: E731
     # headline: sparse K=16, kernel timing on, clocks sampled
     rend.set_timing(False)
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    rend.kernel_times(reset=True)
-    rend.set_timing(True)
-    with ClockSampler(local) as clk:
+    with ClockSampler(local) as clk:      # live before the warm-up
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        rend.kernel_times(reset=True)
+        rend.set_timing(True)
+        clk.mark()
         ms = time_steps(step, args.steps, 0, torch, barrier)
-    rend.set_timing(False)
+        rend.set_timing(False)
     ktimes = rend.kernel_times(reset=True)
     assert rend.sync() == 0
     ms = max_over_ranks(ms)

@@ -1,0 +1,75 @@
+"""Host-side logic of bench.py that needs no GPU: the clock sampler (against a fake
+nvidia-smi) and the rule that DRAM traffic is reported only from a profile taken on the
+current kernel source."""
+import hashlib
+import os
+import stat
+import sys
+import time
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _fake_smi(tmp_path, line):
+    d = tmp_path / "bin"
+    d.mkdir()
+    p = d / "nvidia-smi"
+    p.write_text("#!/bin/sh\nwhile true; do echo \"%s\"; sleep 0.02; done\n" % line)
+    p.chmod(p.stat().st_mode | stat.S_IEXEC)
+    return str(d)
+
+
+def test_clock_sampler_reads_clocks_and_reasons(tmp_path, monkeypatch):
+    line = "0, 2070, 2070, 950.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active"
+    monkeypatch.setenv("PATH", _fake_smi(tmp_path, line))
+    with bench.ClockSampler(0, period_ms=20) as c:
+        time.sleep(0.05)              # a warm-up: its samples are not summarised
+        c.mark()
+        time.sleep(0.1)
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+    assert s["samples"] >= 2
+    assert len(c.lines) > s["samples"]
+
+
+def test_clock_sampler_short_region_still_sampled(tmp_path, monkeypatch):
+    line = "0, 1980, 2070, 1200.0, 0x0, Active, Not Active, Not Active, Not Active"
+    monkeypatch.setenv("PATH", _fake_smi(tmp_path, line))
+    with bench.ClockSampler(0, period_ms=20) as c:
+        pass                          # a region far shorter than the sampling period
+    s = c.summary()
+    assert s["samples"] >= 1 and s["sm_mhz"] == 1980.0
+    assert s["reasons"] == ["hw_slowdown"]
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    with bench.ClockSampler(0) as c:
+        pass
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+
+def test_committed_profile_matches_committed_kernel():
+    # the headline kernel's ncu summary was taken on the source in the tree
+    t = bench.profiled_traffic("mix_sparse_tmem.cu", "mix_sparse_batched_1024x480000_k16.md")
+    assert t == pytest.approx(2.0288e9)
+
+
+def test_traffic_withheld_when_kernel_changed(tmp_path, monkeypatch):
+    (tmp_path / "profiles").mkdir()
+    csrc = tmp_path / "paper_1502_03162_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k.cu").write_text("// kernel v1\n")
+    sha = hashlib.sha256(b"// kernel v1\n").hexdigest()
+    (tmp_path / "profiles" / "k.md").write_text(
+        f"kernel_source_sha256: {sha}\ndram_bytes_per_launch_full_size: 1.5e+09\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("k.cu", "k.md") == pytest.approx(1.5e9)
+    (csrc / "k.cu").write_text("// kernel v2\n")
+    assert bench.profiled_traffic("k.cu", "k.md") is None
+    assert bench.profiled_traffic("k.cu", "missing.md") is None
