@@ -90,11 +90,12 @@ def sources_ar1(rng: np.random.Generator, S: int, L: int, ld: int | None = None,
             out[:, L:] = 0.0
     if L == 0:
         return out
-    zi_scale = coef / np.sqrt(1.0 - coef * coef)
+    # the filter gives y[0] = e[0] + zi: zi = e[0] (1/sqrt(1-c^2) - 1) makes y[0] have the
+    # stationary variance 1/(1-c^2)
+    zi_scale = 1.0 / np.sqrt(1.0 - coef * coef) - 1.0
     for s0 in range(0, S, chunk):
         s1 = min(S, s0 + chunk)
         e = rng.standard_normal((s1 - s0, L), dtype=np.float32)
-        # stationary start: y[0] = e[0]/sqrt(1-c^2)  <=>  initial state c * e[0]/sqrt(1-c^2)
         zi = (zi_scale * e[:, :1]).astype(np.float32)
         y, _ = scipy.signal.lfilter([1.0], [1.0, -coef], e, axis=1, zi=zi)
         out[s0:s1, :L] = y.astype(np.float32)
@@ -198,8 +199,10 @@ def hrir_set(seed: int, **kw):
 
 
 def trajectories(rng: np.random.Generator, S: int, n_seg: int):
-    """Moving-source directions per (source, segment): smooth random walks over the grid's
-    azimuth/elevation range.  Returns (az, el) radians [S][n_seg]."""
+    """Moving-source directions per (source, segment): each source starts at a uniform
+    direction in the grid's azimuth/elevation range and moves at a constant random velocity
+    of at most 0.5 degrees per segment in each angle, reflected at the range's edges.
+    Returns (az, el) radians [S][n_seg]."""
     az_lo, az_hi = np.deg2rad(-80.0), np.deg2rad(80.0)
     el_lo, el_hi = np.deg2rad(-45.0), np.deg2rad(230.0)
     az0 = rng.uniform(az_lo, az_hi, S)
