@@ -109,7 +109,62 @@ def _stream_handle(stream) -> int:
 
 def _dtype_code(t) -> int:
     import torch
-    return {torch.float32: HRIR_F32, torch.bfloat16: HRIR_BF16, torch.float16: HRIR_F16}[t.dtype]
+    codes = {torch.float32: HRIR_F32, torch.bfloat16: HRIR_BF16, torch.float16: HRIR_F16}
+    _require(t.dtype in codes, f"source dtype {t.dtype}: expected float32, bfloat16 or float16")
+    return codes[t.dtype]
+
+
+# ---------------------------------------------------------------------------------------
+# argument checks: the C ABI receives raw pointers and sizes, so every extent a kernel will
+# read or write is checked here against the tensor that backs it (ValueError otherwise)
+# ---------------------------------------------------------------------------------------
+def _require(cond, msg: str) -> None:
+    if not cond:
+        raise ValueError(msg)
+
+
+def _check_tensor(t, name: str, *, cuda: bool, dtypes, dim=None, shape=None, min_shape=None,
+                  numel=None, contiguous=False, unit_stride=False) -> None:
+    """t must be a tensor on the stated side (CUDA or host) with one of `dtypes`; optional
+    exact rank, exact or minimum shape, exact element count, contiguity, and unit stride in
+    its last dimension (empty tensors pass the layout checks)."""
+    _require(t is not None and hasattr(t, "data_ptr") and hasattr(t, "dtype"),
+             f"{name}: expected a torch tensor")
+    _require(bool(t.is_cuda) == cuda, f"{name}: expected a {'CUDA' if cuda else 'host (CPU)'} tensor")
+    _require(t.dtype in dtypes, f"{name}: dtype {t.dtype}, expected one of {list(dtypes)}")
+    if dim is not None:
+        _require(t.dim() == dim, f"{name}: {t.dim()} dimensions, expected {dim}")
+    if shape is not None:
+        _require(tuple(t.shape) == tuple(shape), f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if min_shape is not None:
+        _require(t.dim() == len(min_shape) and all(a >= b for a, b in zip(t.shape, min_shape)),
+                 f"{name}: shape {tuple(t.shape)}, expected at least {tuple(min_shape)}")
+    if numel is not None:
+        _require(t.numel() == numel, f"{name}: {t.numel()} elements, expected {numel}")
+    if contiguous:
+        _require(t.numel() == 0 or t.is_contiguous(), f"{name}: expected a contiguous tensor")
+    if unit_stride:
+        _require(t.numel() == 0 or t.stride(-1) == 1, f"{name}: last dimension must have stride 1")
+
+
+def _src_dtypes():
+    import torch
+    return (torch.float32, torch.bfloat16, torch.float16)
+
+
+def _index_dtypes():
+    """Tap index tensors: int16 holding the uint16 indices (all < 2048), or uint16."""
+    import torch
+    return tuple(t for t in (torch.int16, getattr(torch, "uint16", None)) if t is not None)
+
+
+def _src_extent(src, length):
+    """(S, ld, L) of a [S][ld] source batch rendered over its first L samples."""
+    S = src.shape[0]
+    ld = src.stride(0) if S > 1 else src.shape[1]
+    L = src.shape[1] if length is None else int(length)
+    _require(0 <= L <= src.shape[1], f"length {L} outside the source rows' {src.shape[1]} samples")
+    return S, ld, L
 
 
 # ---------------------------------------------------------------------------------------
@@ -152,16 +207,20 @@ def hrir_topk_pack(ctx, g, k: int, idx=None, w=None, nnz=None, stream=None):
     holding the uint16 indices (all < 2048, so the values read the same), w float32, nnz
     uint8."""
     import torch
-    assert g.is_cuda and g.dtype == torch.float32 and g.is_contiguous()
+    _check_tensor(g, "g", cuda=True, dtypes=(torch.float32,), contiguous=True)
+    _require(g.dim() >= 1 and int(k) >= 0, "g needs a last (filter) dimension and k >= 0")
     refl_len = g.shape[-1]
     lead = tuple(g.shape[:-1])
     rows = int(np.prod(lead)) if lead else 1
     if idx is None:
         idx = torch.empty(lead + (k,), dtype=torch.int16, device=g.device)   # uint16 payload
+    _check_tensor(idx, "idx", cuda=True, dtypes=_index_dtypes(), numel=rows * k, contiguous=True)
     if w is None:
         w = torch.empty(lead + (k,), dtype=torch.float32, device=g.device)
+    _check_tensor(w, "w", cuda=True, dtypes=(torch.float32,), numel=rows * k, contiguous=True)
     if nnz is None:
         nnz = torch.empty(lead, dtype=torch.uint8, device=g.device)
+    _check_tensor(nnz, "nnz", cuda=True, dtypes=(torch.uint8,), numel=rows, contiguous=True)
     rc = load_library().hrir_topk_pack(ctx, rows, refl_len, k, g.data_ptr(), idx.data_ptr(),
                                        w.data_ptr(), nnz.data_ptr(), _stream_handle(stream))
     _check(ctx, rc)
@@ -171,11 +230,19 @@ def hrir_topk_pack(ctx, g, k: int, idx=None, w=None, nnz=None, stream=None):
 def hrir_load_filters(ctx, tap_idx, tap_w, tap_nnz, refl_len: int, res, fft_size: int = 0):
     """Host numpy arrays: tap_idx uint16 [n_dirs][2][k_max], tap_w float32, tap_nnz uint8
     [n_dirs][2], res float32 [2][Lf]."""
-    tap_idx = np.ascontiguousarray(tap_idx, dtype=np.uint16)
+    raw = np.asarray(tap_idx)
+    _require(raw.ndim == 3, f"tap_idx: shape {raw.shape}, expected [n_dirs][n_ears][k_max]")
+    if raw.dtype != np.uint16 and raw.size:
+        _require(np.issubdtype(raw.dtype, np.integer) and raw.min() >= 0 and raw.max() <= 0xFFFF,
+                 "tap_idx: indices must be integers in [0, 65535]")
+    tap_idx = np.ascontiguousarray(raw, dtype=np.uint16)
     tap_w = np.ascontiguousarray(tap_w, dtype=np.float32)
     tap_nnz = np.ascontiguousarray(tap_nnz, dtype=np.uint8)
     res = np.ascontiguousarray(res, dtype=np.float32)
     n_dirs, n_ears, k_max = tap_idx.shape
+    _require(tap_w.shape == tap_idx.shape, f"tap_w: shape {tap_w.shape}, expected {tap_idx.shape}")
+    _require(tap_nnz.shape == (n_dirs, n_ears), f"tap_nnz: shape {tap_nnz.shape}, expected {(n_dirs, n_ears)}")
+    _require(res.ndim == 2 and res.shape[0] == n_ears, f"res: shape {res.shape}, expected [{n_ears}][Lf]")
     rc = load_library().hrir_load_filters(
         ctx, n_dirs, n_ears, refl_len, k_max, tap_idx.ctypes.data, tap_w.ctypes.data,
         tap_nnz.ctypes.data, res.shape[1], res.ctypes.data, fft_size)
@@ -192,15 +259,15 @@ def hrir_render_batch(ctx, src, dirs, mode="sparse", full=True, length=None, out
     """src: CUDA [S][ld] float32/bfloat16/float16; dirs: CUDA int32 [S].
     Returns out: CUDA float32 [2][out_len] (or the given buffer)."""
     import torch
-    assert src.is_cuda and src.dim() == 2 and (src.numel() == 0 or src.stride(1) == 1)
-    S = src.shape[0]
-    ld = src.stride(0) if S > 1 else src.shape[1]
-    L = src.shape[1] if length is None else int(length)
+    _check_tensor(src, "src", cuda=True, dtypes=_src_dtypes(), dim=2, unit_stride=True)
+    S, ld, L = _src_extent(src, length)
+    _check_tensor(dirs, "dirs", cuda=True, dtypes=(torch.int32,), contiguous=True)
+    _require(dirs.numel() >= S, f"dirs: {dirs.numel()} entries for {S} sources")
     out_len = hrir_out_len(ctx, L, full)
     if out is None:
         out = torch.empty((2, max(out_len, 1)), dtype=torch.float32, device=src.device)
-    assert out.is_cuda and out.dtype == torch.float32 and out.stride(1) == 1
-    assert dirs.is_cuda and dirs.dtype == torch.int32 and (dirs.numel() == 0 or dirs.is_contiguous())
+    _check_tensor(out, "out", cuda=True, dtypes=(torch.float32,), min_shape=(2, out_len),
+                  unit_stride=True)
     rc = load_library().hrir_render_batch(
         ctx, S, L, ld, _dtype_code(src), src.data_ptr(), dirs.data_ptr(),
         MODES[mode] if isinstance(mode, str) else int(mode), int(full), out.data_ptr(),
@@ -214,15 +281,17 @@ def hrir_render_batch_host(ctx, src, dirs, mode="sparse", full=True, length=None
     """src: CPU tensor [S][ld] (pinned for speed); dirs: CPU int32 [S].  Synchronous; returns
     a CPU float32 [2][out_len] tensor."""
     import torch
-    assert (not src.is_cuda) and src.dim() == 2 and (src.numel() == 0 or src.stride(1) == 1)
-    S = src.shape[0]
-    ld = src.stride(0) if S > 1 else src.shape[1]
-    L = src.shape[1] if length is None else int(length)
+    _check_tensor(src, "src", cuda=False, dtypes=_src_dtypes(), dim=2, unit_stride=True)
+    S, ld, L = _src_extent(src, length)
+    _check_tensor(dirs, "dirs", cuda=False, dtypes=(torch.int32,))
+    dirs = dirs.contiguous()
+    _require(dirs.numel() >= S, f"dirs: {dirs.numel()} entries for {S} sources")
     out_len = hrir_out_len(ctx, L, full)
     if out is None:
         out = torch.empty((2, max(out_len, 1)), dtype=torch.float32,
                           pin_memory=src.is_pinned())
-    dirs = dirs.contiguous()
+    _check_tensor(out, "out", cuda=False, dtypes=(torch.float32,), min_shape=(2, out_len),
+                  unit_stride=True)
     rc = load_library().hrir_render_batch_host(
         ctx, S, L, ld, _dtype_code(src), src.data_ptr(), dirs.data_ptr(),
         MODES[mode] if isinstance(mode, str) else int(mode), int(full), out.data_ptr(),
@@ -236,12 +305,14 @@ def hrir_render_batch_noalloc(ctx, src, dirs, out, mode="sparse", full=True, len
     """The allocation-free variant of hrir_render_batch: the caller passes every buffer,
     including `out` (CUDA float32 [2][>= out_len]); the library uses its fixed 32 MiB device
     scratch array and allocates nothing.  Returns out[:, :out_len]."""
-    assert src.is_cuda and src.dim() == 2 and (src.numel() == 0 or src.stride(1) == 1)
-    S = src.shape[0]
-    ld = src.stride(0) if S > 1 else src.shape[1]
-    L = src.shape[1] if length is None else int(length)
+    import torch
+    _check_tensor(src, "src", cuda=True, dtypes=_src_dtypes(), dim=2, unit_stride=True)
+    S, ld, L = _src_extent(src, length)
+    _check_tensor(dirs, "dirs", cuda=True, dtypes=(torch.int32,), contiguous=True)
+    _require(dirs.numel() >= S, f"dirs: {dirs.numel()} entries for {S} sources")
     out_len = hrir_out_len(ctx, L, full)
-    assert out.is_cuda and out.stride(1) == 1
+    _check_tensor(out, "out", cuda=True, dtypes=(torch.float32,), min_shape=(2, out_len),
+                  unit_stride=True)
     rc = load_library().hrir_render_batch_noalloc(
         ctx, S, L, ld, _dtype_code(src), src.data_ptr(), dirs.data_ptr(),
         MODES[mode] if isinstance(mode, str) else int(mode), int(full), out.data_ptr(),
@@ -261,10 +332,12 @@ def hrir_stream_admit(ctx, req_id: int, session: int, src, direction: int) -> in
     status: HRIR_OK, or HRIR_EBUSY / HRIR_ENOMEM when the request was not admitted now.
     Other errors raise."""
     if hasattr(src, "data_ptr"):
-        assert src.dtype.__str__() == "torch.float32" and src.is_contiguous() and not src.is_cuda
+        import torch
+        _check_tensor(src, "src", cuda=False, dtypes=(torch.float32,), contiguous=True)
         ptr, n = src.data_ptr(), src.numel()
     else:
-        assert src.dtype == np.float32 and src.flags.c_contiguous
+        _require(isinstance(src, np.ndarray) and src.dtype == np.float32 and src.flags.c_contiguous,
+                 "src: expected a contiguous float32 numpy array or CPU tensor")
         ptr, n = src.ctypes.data, src.size
     rc = load_library().hrir_stream_admit(ctx, int(req_id), int(session), ptr, int(n),
                                           int(direction))
@@ -342,11 +415,9 @@ def hrir_mlp_act_stride(refl_len: int) -> int:
     return load_library().hrir_mlp_act_stride(refl_len)
 
 
-def _f32_cuda(t, shape=None):
+def _f32_cuda(t, shape=None, name="tensor"):
     import torch
-    assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
-    if shape is not None:
-        assert tuple(t.shape) == tuple(shape), (tuple(t.shape), shape)
+    _check_tensor(t, name, cuda=True, dtypes=(torch.float32,), shape=shape, contiguous=True)
     return t.data_ptr()
 
 
@@ -414,17 +485,20 @@ def hrir_render_moving(ctx, src, tap_idx, tap_w, tap_nnz, seg_len: int, full=Tru
     """src: CUDA float32 [S][ld]; tap tables CUDA [S][n_seg][2][k] (idx int16 holding uint16,
     w float32) and nnz uint8 [S][n_seg][2].  Returns out CUDA float32 [2][out_len]."""
     import torch
-    assert src.is_cuda and src.dtype == torch.float32 and src.dim() == 2 and src.stride(1) == 1
-    S = src.shape[0]
-    ld = src.stride(0) if S > 1 else src.shape[1]
-    L = src.shape[1] if length is None else int(length)
+    _check_tensor(src, "src", cuda=True, dtypes=(torch.float32,), dim=2, unit_stride=True)
+    S, ld, L = _src_extent(src, length)
+    _check_tensor(tap_idx, "tap_idx", cuda=True, dtypes=_index_dtypes(), dim=4, contiguous=True)
     n_seg, k = tap_idx.shape[1], tap_idx.shape[3]
-    assert tuple(tap_idx.shape) == (S, n_seg, 2, k) and tap_idx.is_contiguous()
-    assert tuple(tap_w.shape) == (S, n_seg, 2, k) and tap_w.is_contiguous()
-    assert tuple(tap_nnz.shape) == (S, n_seg, 2) and tap_nnz.is_contiguous()
+    _check_tensor(tap_idx, "tap_idx", cuda=True, dtypes=_index_dtypes(), shape=(S, n_seg, 2, k))
+    _check_tensor(tap_w, "tap_w", cuda=True, dtypes=(torch.float32,), shape=(S, n_seg, 2, k),
+                  contiguous=True)
+    _check_tensor(tap_nnz, "tap_nnz", cuda=True, dtypes=(torch.uint8,), shape=(S, n_seg, 2),
+                  contiguous=True)
     out_len = hrir_out_len(ctx, L, full)
     if out is None:
         out = torch.empty((2, max(out_len, 1)), dtype=torch.float32, device=src.device)
+    _check_tensor(out, "out", cuda=True, dtypes=(torch.float32,), min_shape=(2, out_len),
+                  unit_stride=True)
     rc = load_library().hrir_render_moving(
         ctx, S, L, ld, src.data_ptr(), n_seg, int(seg_len), k, tap_idx.data_ptr(),
         tap_w.data_ptr(), tap_nnz.data_ptr(), int(full), out.data_ptr(), out.stride(0),
@@ -437,18 +511,18 @@ def hrir_resonance_per_source(ctx, src, full=True, length=None, out=None, stream
     """src: CUDA bfloat16/float16 [S][ld].  Returns u: CUDA float32 [S][2][out_len] with
     u[s, e] = y_s * f_e (the loaded resonance), computed on the tensor cores."""
     import torch
-    assert src.is_cuda and src.dim() == 2 and src.stride(1) == 1
-    assert src.dtype in (torch.bfloat16, torch.float16)
-    S = src.shape[0]
-    ld = src.stride(0) if S > 1 else src.shape[1]
-    L = src.shape[1] if length is None else int(length)
+    _check_tensor(src, "src", cuda=True, dtypes=(torch.bfloat16, torch.float16), dim=2,
+                  unit_stride=True)
+    S, ld, L = _src_extent(src, length)
     res_len = _res_len(ctx)
     out_len = (L + res_len - 1 if L > 0 else 0) if full else L
     if out is None:
         out = torch.empty((S, 2, max((out_len + 3) // 4 * 4, 4)), dtype=torch.float32,
                           device=src.device)
-    assert out.is_cuda and out.dtype == torch.float32 and out.stride(2) == 1
-    assert out.stride(0) == 2 * out.stride(1)
+    _check_tensor(out, "out", cuda=True, dtypes=(torch.float32,), min_shape=(S, 2, out_len),
+                  unit_stride=True)
+    _require(out.numel() == 0 or out.stride(0) == 2 * out.stride(1),
+             "out: the two ears of a source must be adjacent rows ([S][2][len] layout)")
     rc = load_library().hrir_resonance_per_source(ctx, S, L, ld, _dtype_code(src), src.data_ptr(),
                                                   int(full), out.data_ptr(), out.stride(1),
                                                   _stream_handle(stream))

@@ -55,5 +55,5 @@ def test_resonance_gemm_rejects_fp32_sources(rend):
     _, idx, w, nnz, res = tables(rng, 4, 16)
     rend.load_filters(idx, w, nnz, 200, res)
     y = torch.zeros((2, 64), device="cuda")
-    with pytest.raises(AssertionError):
+    with pytest.raises(ValueError):
         hrir.hrir_resonance_per_source(rend.ctx, y)
