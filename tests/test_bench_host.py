@@ -73,3 +73,18 @@ def test_traffic_withheld_when_kernel_changed(tmp_path, monkeypatch):
     (csrc / "k.cu").write_text("// kernel v2\n")
     assert bench.profiled_traffic("k.cu", "k.md") is None
     assert bench.profiled_traffic("k.cu", "missing.md") is None
+
+
+def test_profile_summaries_run_committed_files_only():
+    import re
+    prof = os.path.join(ROOT, "profiles")
+    names = [f for f in os.listdir(prof) if f.endswith((".md", ".txt"))]
+    assert names
+    for f in names:
+        text = open(os.path.join(prof, f)).read()
+        scripts = re.findall(r"python3?\s+(?:-m\s+)?(\S+\.py)", text)
+        assert scripts, f"{f}: no command"
+        for s in scripts:
+            assert os.path.isfile(os.path.join(ROOT, s)), f"{f}: {s} is not in the repository"
+            assert not s.startswith("_work"), f"{f}: {s} is a working file"
+        assert "--clock-control none" in text or "ncu" not in text, f"{f}: ncu without clock control"
