@@ -57,3 +57,22 @@ def test_binding_fails_loudly_without_library(tmp_path):
             mod.load_library(str(tmp_path / "missing.so"))
     finally:
         mod._lib = saved
+
+
+def test_every_declared_function_is_documented():
+    # each declaration in the header sits below a comment block that documents it (the
+    # block may document a group of related calls declared together)
+    lines = open(HEADER).read().splitlines()
+    decl = re.compile(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(hrir_[a-z0-9_]+)\s*\(")
+    for i, ln in enumerate(lines):
+        m = decl.match(ln)
+        if not m:
+            continue
+        j = i - 1
+        # skip continuation lines, neighbouring declarations and a typedef the block also
+        # documents (the kernel-family enum of the timing calls)
+        while j >= 0 and not lines[j].rstrip().endswith("*/") and (
+                decl.match(lines[j]) or lines[j].startswith((" ", "\t", "typedef", "}"))
+                or (lines[j].strip() == "" and j > 0 and lines[j - 1].startswith("}"))):
+            j -= 1
+        assert j >= 0 and lines[j].rstrip().endswith("*/"), f"{m.group(1)} has no doc comment"
