@@ -20,7 +20,7 @@ def _fake_smi(tmp_path, line):
     p = d / "nvidia-smi"
     p.write_text("#!/bin/sh\nwhile true; do echo \"%s\"; sleep 0.02; done\n" % line)
     p.chmod(p.stat().st_mode | stat.S_IEXEC)
-    return str(d)
+    return str(d) + os.pathsep + os.environ.get("PATH", "")   # the fake first; `sleep` still found
 
 
 def test_clock_sampler_reads_clocks_and_reasons(tmp_path, monkeypatch):
