@@ -1,0 +1,132 @@
+"""Property-based pins of the oracle (hypothesis): the definitions and invariants the paper
+fixes, on generated inputs rather than fixed seeds.
+
+  * direct convolution (Sec. I footnote 2) equals the brute-force double sum and is
+    commutative and bilinear;
+  * sparse convolution (Eq. 2) equals direct convolution with the zero-filled filter;
+  * the radix-2 FFT equals the O(P^2) DFT, and FFT convolution (footnote 3) equals direct
+    convolution;
+  * top-K keeps the K largest strictly positive entries, larger value first and the smaller
+    index on ties, stored in ascending index order (brute force by sorting);
+  * the cascade (y * g) * f renders like y * (f * g) (Eqs. 1-2) and the mix is linear in the
+    sources.
+"""
+import numpy as np
+import pytest
+
+hypothesis = pytest.importorskip("hypothesis")
+from hypothesis import given, settings, strategies as st  # noqa: E402
+from hypothesis.extra import numpy as hnp  # noqa: E402
+
+import oracle  # noqa: E402
+
+SETTINGS = settings(max_examples=60, deadline=None)
+finite = st.floats(-4.0, 4.0, allow_nan=False, allow_infinity=False, width=64)
+
+
+def vec(min_size=1, max_size=40):
+    return hnp.arrays(np.float64, st.integers(min_size, max_size), elements=finite)
+
+
+@SETTINGS
+@given(vec(), vec())
+def test_conv_direct_is_the_double_sum(x, y):
+    out = oracle.conv_direct(x, y)
+    ref = np.zeros(x.size + y.size - 1)
+    for j in range(x.size):
+        for m in range(y.size):
+            ref[j + m] += x[j] * y[m]
+    np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(oracle.conv_direct(y, x), out, rtol=1e-12, atol=1e-12)
+
+
+@SETTINGS
+@given(vec(), vec(), vec(), st.floats(-3, 3, allow_nan=False))
+def test_conv_direct_is_bilinear(x, y, z, a):
+    n = min(y.size, z.size)
+    y, z = y[:n], z[:n]
+    lhs = oracle.conv_direct(x, a * y + z)
+    rhs = a * oracle.conv_direct(x, y) + oracle.conv_direct(x, z)
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-9, atol=1e-9)
+
+
+@SETTINGS
+@given(st.integers(1, 60), st.data())
+def test_conv_sparse_equals_zero_filled_dense(refl_len, data):
+    k = data.draw(st.integers(0, refl_len))
+    idx = np.array(sorted(data.draw(st.sets(st.integers(0, refl_len - 1), min_size=k, max_size=k))),
+                   dtype=np.int32)
+    w = data.draw(hnp.arrays(np.float64, idx.size, elements=st.floats(0, 3, allow_nan=False)))
+    y = data.draw(vec(1, 50))
+    g = np.zeros(refl_len)
+    g[idx] = w
+    np.testing.assert_allclose(oracle.conv_sparse(idx, w, y, refl_len), oracle.conv_direct(g, y),
+                               rtol=1e-12, atol=1e-12)
+
+
+@SETTINGS
+@given(st.integers(0, 6), st.data())
+def test_fft_equals_dft_and_inverts(log2p, data):
+    p = 1 << log2p
+    re = data.draw(hnp.arrays(np.float64, p, elements=finite))
+    im = data.draw(hnp.arrays(np.float64, p, elements=finite))
+    x = re + 1j * im
+    X = oracle.fft(x)
+    np.testing.assert_allclose(X, oracle.dft(x), rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(oracle.fft(X, inverse=True), x, rtol=1e-10, atol=1e-10)
+
+
+@SETTINGS
+@given(vec(1, 70), vec(1, 70))
+def test_conv_fft_equals_direct(x, y):
+    d = oracle.conv_direct(x, y)
+    scale = max(1.0, np.abs(x).sum() * np.abs(y).max())
+    np.testing.assert_allclose(oracle.conv_fft(x, y), d, rtol=0, atol=1e-11 * scale)
+
+
+def _topk_brute(row, k):
+    cand = [(-float(v), i) for i, v in enumerate(row) if v > 0]      # NaN > 0 is False
+    cand.sort()
+    keep = sorted(i for _, i in cand[:k])
+    return keep
+
+
+@settings(max_examples=120, deadline=None)
+@given(st.integers(1, 48), st.integers(0, 20), st.data())
+def test_topk_against_sorting(refl_len, k, data):
+    # few distinct values so that ties are common; negatives, zeros and NaN never selected
+    pool = st.sampled_from([0.0, -1.0, float("nan"), 0.25, 0.5, 1.0, 1.5, 2.0, 1e-30, 3.0e5])
+    row = np.array(data.draw(st.lists(pool, min_size=refl_len, max_size=refl_len)), np.float32)
+    idx, w, nnz = oracle.topk(row[None], k)
+    keep = _topk_brute(row, k)
+    assert int(nnz[0]) == len(keep)
+    assert list(idx[0, :len(keep)]) == keep
+    np.testing.assert_array_equal(w[0, :len(keep)], row[keep])
+    assert not idx[0, len(keep):].any() and not w[0, len(keep):].any()
+
+
+@settings(max_examples=25, deadline=None)
+@given(st.integers(1, 4), st.integers(1, 300), st.integers(1, 8), st.data())
+def test_render_cascade_and_linearity(S, L, k, data):
+    rng = np.random.default_rng(data.draw(st.integers(0, 2 ** 31 - 1)))
+    refl_len, res_len, n_dirs = 40, 7, 3
+    G = rng.random((n_dirs, 2, refl_len)) * (rng.random((n_dirs, 2, refl_len)) < 0.3)
+    idx, w, nnz = oracle.topk(G.astype(np.float32), k)
+    res = rng.standard_normal((2, res_len)).astype(np.float32)
+    y = rng.standard_normal((S, L)).astype(np.float32)
+    dirs = rng.integers(0, n_dirs, S).astype(np.int32)
+    out = oracle.render_sparse(y, dirs, idx, w, nnz, refl_len, res)
+    # Eq. 1-2: the cascade equals convolution with the dense HRIR f * g, summed over sources
+    ref = np.zeros((2, L + refl_len + res_len - 2))
+    for s in range(S):
+        for e in range(2):
+            g = np.zeros(refl_len)
+            n = int(nnz[dirs[s], e])
+            g[idx[dirs[s], e, :n].astype(int)] = w[dirs[s], e, :n]
+            h = np.convolve(res[e].astype(np.float64), g)
+            ref[e] += np.convolve(y[s].astype(np.float64), h)
+    np.testing.assert_allclose(out, ref, rtol=1e-10, atol=1e-10)
+    # linear in the sources
+    parts = sum(oracle.render_sparse(y[s:s + 1], dirs[s:s + 1], idx, w, nnz, refl_len, res)
+                for s in range(S))
+    np.testing.assert_allclose(out, parts, rtol=1e-10, atol=1e-10)
