@@ -9,7 +9,11 @@ fixes, on generated inputs rather than fixed seeds.
   * top-K keeps the K largest strictly positive entries, larger value first and the smaller
     index on ties, stored in ascending index order (brute force by sorting);
   * the cascade (y * g) * f renders like y * (f * g) (Eqs. 1-2) and the mix is linear in the
-    sources.
+    sources;
+  * the multiplicative reflection update (Eq. 4) keeps G >= 0 (zeros stay zero) and never
+    increases the residual; the L1-NNLS solution (Eq. 14) is feasible, meets the KKT
+    conditions and no nearby feasible point has a lower objective; the resonance solve
+    (Eqs. 9-11) zeroes the gradient of the least-squares objective.
 """
 import numpy as np
 import pytest
@@ -130,3 +134,59 @@ def test_render_cascade_and_linearity(S, L, k, data):
     parts = sum(oracle.render_sparse(y[s:s + 1], dirs[s:s + 1], idx, w, nnz, refl_len, res)
                 for s in range(S))
     np.testing.assert_allclose(out, parts, rtol=1e-10, atol=1e-10)
+
+
+# ---- filter production (Sec. III) ----------------------------------------------------------
+from oracle import factorize as fz  # noqa: E402
+
+
+@settings(max_examples=40, deadline=None)
+@given(st.integers(0, 2 ** 31 - 1), st.integers(3, 12), st.integers(2, 8), st.integers(1, 6))
+def test_reflection_update_keeps_sign_and_never_increases_the_residual(seed, N, Lg, Lf):
+    rng = np.random.default_rng(seed)
+    M = Lf + Lg - 1
+    X = rng.standard_normal((M, N))
+    f = rng.standard_normal(Lf)
+    F = fz.toeplitz_filter_matrix(f, Lg)
+    G = rng.random((N, Lg)) * (rng.random((N, Lg)) < 0.8)
+    r0 = float(np.sum((X - F @ G.T) ** 2))
+    for _ in range(5):
+        G1 = fz.update_reflections(X, F, G)
+        assert np.all(G1 >= 0) and np.all(G1[G == 0] == 0)       # zeros stay zero (Eq. 4)
+        r1 = float(np.sum((X - F @ G1.T) ** 2))
+        assert r1 <= r0 * (1 + 1e-12) + 1e-12
+        G, r0 = G1, r1
+
+
+@settings(max_examples=40, deadline=None)
+@given(st.integers(0, 2 ** 31 - 1), st.integers(2, 8), st.integers(1, 5),
+       st.floats(0.0, 2.0, allow_nan=False))
+def test_l1_nnls_is_the_constrained_minimiser(seed, Lg, Lf, lam):
+    rng = np.random.default_rng(seed)
+    f = rng.standard_normal(Lf)
+    f[0] = 1.0 + abs(f[0])                                       # full column rank
+    F = fz.toeplitz_filter_matrix(f, Lg)
+    x = rng.standard_normal(F.shape[0])
+    g = fz.l1_nnls(F, x, lam)
+    assert np.all(g >= 0)
+    assert fz.kkt_violation(F, x, g, lam) <= 1e-8 * max(1.0, np.abs(F.T @ x).max())
+    obj = lambda v: float(np.sum((F @ v - x) ** 2) + lam * np.sum(v))  # noqa: E731
+    for _ in range(20):                                          # no feasible point is better
+        v = np.maximum(0.0, g + 0.1 * rng.standard_normal(Lg))
+        assert obj(g) <= obj(v) + 1e-10
+
+
+@settings(max_examples=40, deadline=None)
+@given(st.integers(0, 2 ** 31 - 1), st.integers(2, 10), st.integers(1, 6), st.integers(1, 5))
+def test_resonance_solve_zeroes_the_gradient(seed, N, Lg, Lf):
+    rng = np.random.default_rng(seed)
+    M = Lf + Lg - 1
+    X = rng.standard_normal((M, N))
+    G = rng.random((N, Lg)) + 0.1
+    f = fz.solve_resonance(X, G, Lf)
+    # d/df sum_i ||X_i - C(g_i) f||^2 = -2 sum_i C(g_i)^T (X_i - C(g_i) f) = 0
+    grad = np.zeros(Lf)
+    for i in range(N):
+        C = fz.conv_matrix(G[i], Lf)
+        grad += C.T @ (X[:, i] - C @ f)
+    assert np.abs(grad).max() <= 1e-9 * max(1.0, np.abs(X).max() * N)
