@@ -13,7 +13,9 @@ fixes, on generated inputs rather than fixed seeds.
   * the multiplicative reflection update (Eq. 4) keeps G >= 0 (zeros stay zero) and never
     increases the residual; the L1-NNLS solution (Eq. 14) is feasible, meets the KKT
     conditions and no nearby feasible point has a lower objective; the resonance solve
-    (Eqs. 9-11) zeroes the gradient of the least-squares objective.
+    (Eqs. 9-11) zeroes the gradient of the least-squares objective;
+  * the moving-source render is the per-segment linear crossfade between consecutive
+    segments' filters (brute force with dense filters and numpy.convolve).
 """
 import numpy as np
 import pytest
@@ -190,3 +192,36 @@ def test_resonance_solve_zeroes_the_gradient(seed, N, Lg, Lf):
         C = fz.conv_matrix(G[i], Lf)
         grad += C.T @ (X[:, i] - C @ f)
     assert np.abs(grad).max() <= 1e-9 * max(1.0, np.abs(X).max() * N)
+
+
+@settings(max_examples=25, deadline=None)
+@given(st.integers(0, 2 ** 31 - 1), st.integers(1, 3), st.integers(1, 400), st.sampled_from([8, 32, 100]))
+def test_moving_render_is_the_segment_crossfade(seed, S, L, seg_len):
+    # brute force with dense filters and numpy.convolve: in segment j >= 1 the reflection output
+    # moves linearly from the previous segment's filter to the current one, a = (n - j seg + 1) / seg
+    rng = np.random.default_rng(seed)
+    refl_len, res_len, k = 30, 5, 4
+    n_seg = (L + seg_len - 1) // seg_len
+    G = rng.random((S, n_seg, 2, refl_len)) * (rng.random((S, n_seg, 2, refl_len)) < 0.4)
+    idx, w, nnz = oracle.topk(G.astype(np.float32), k)
+    res = rng.standard_normal((2, res_len)).astype(np.float32)
+    y = rng.standard_normal((S, L)).astype(np.float32)
+    out = oracle.render_moving(y, idx, w, nnz, seg_len, refl_len, res)
+    n_z = L + refl_len - 1
+    z = np.zeros((2, n_z))
+    for s in range(S):
+        for e in range(2):
+            full = []
+            for j in range(n_seg):
+                g = np.zeros(refl_len)
+                g[idx[s, j, e, :nnz[s, j, e]].astype(int)] = w[s, j, e, :nnz[s, j, e]]
+                full.append(np.convolve(y[s].astype(np.float64), g))
+            for n in range(n_z):
+                j = min(n // seg_len, n_seg - 1)
+                if 1 <= n // seg_len < n_seg:
+                    a = (n - j * seg_len + 1) / seg_len
+                    z[e, n] += (1 - a) * full[j - 1][n] + a * full[j][n]
+                else:
+                    z[e, n] += full[j][n]
+    ref = np.stack([np.convolve(res[e].astype(np.float64), z[e]) for e in range(2)])
+    np.testing.assert_allclose(out, ref, rtol=1e-10, atol=1e-10)
