@@ -26,7 +26,7 @@ from hypothesis.extra import numpy as hnp  # noqa: E402
 
 import oracle  # noqa: E402
 
-SETTINGS = settings(max_examples=60, deadline=None)
+SETTINGS = settings(max_examples=60, deadline=None, derandomize=True)
 finite = st.floats(-4.0, 4.0, allow_nan=False, allow_infinity=False, width=64)
 
 
@@ -97,7 +97,7 @@ def _topk_brute(row, k):
     return keep
 
 
-@settings(max_examples=120, deadline=None)
+@settings(max_examples=120, deadline=None, derandomize=True)
 @given(st.integers(1, 48), st.integers(0, 20), st.data())
 def test_topk_against_sorting(refl_len, k, data):
     # few distinct values so that ties are common; negatives, zeros and NaN never selected
@@ -111,7 +111,7 @@ def test_topk_against_sorting(refl_len, k, data):
     assert not idx[0, len(keep):].any() and not w[0, len(keep):].any()
 
 
-@settings(max_examples=25, deadline=None)
+@settings(max_examples=25, deadline=None, derandomize=True)
 @given(st.integers(1, 4), st.integers(1, 300), st.integers(1, 8), st.data())
 def test_render_cascade_and_linearity(S, L, k, data):
     rng = np.random.default_rng(data.draw(st.integers(0, 2 ** 31 - 1)))
@@ -142,7 +142,7 @@ def test_render_cascade_and_linearity(S, L, k, data):
 from oracle import factorize as fz  # noqa: E402
 
 
-@settings(max_examples=40, deadline=None)
+@settings(max_examples=40, deadline=None, derandomize=True)
 @given(st.integers(0, 2 ** 31 - 1), st.integers(3, 12), st.integers(2, 8), st.integers(1, 6))
 def test_reflection_update_keeps_sign_and_never_increases_the_residual(seed, N, Lg, Lf):
     rng = np.random.default_rng(seed)
@@ -160,7 +160,7 @@ def test_reflection_update_keeps_sign_and_never_increases_the_residual(seed, N, 
         G, r0 = G1, r1
 
 
-@settings(max_examples=40, deadline=None)
+@settings(max_examples=40, deadline=None, derandomize=True)
 @given(st.integers(0, 2 ** 31 - 1), st.integers(2, 8), st.integers(1, 5),
        st.floats(0.0, 2.0, allow_nan=False))
 def test_l1_nnls_is_the_constrained_minimiser(seed, Lg, Lf, lam):
@@ -178,7 +178,7 @@ def test_l1_nnls_is_the_constrained_minimiser(seed, Lg, Lf, lam):
         assert obj(g) <= obj(v) + 1e-10
 
 
-@settings(max_examples=40, deadline=None)
+@settings(max_examples=40, deadline=None, derandomize=True)
 @given(st.integers(0, 2 ** 31 - 1), st.integers(2, 10), st.integers(1, 6), st.integers(1, 5))
 def test_resonance_solve_zeroes_the_gradient(seed, N, Lg, Lf):
     rng = np.random.default_rng(seed)
@@ -194,7 +194,7 @@ def test_resonance_solve_zeroes_the_gradient(seed, N, Lg, Lf):
     assert np.abs(grad).max() <= 1e-9 * max(1.0, np.abs(X).max() * N)
 
 
-@settings(max_examples=25, deadline=None)
+@settings(max_examples=25, deadline=None, derandomize=True)
 @given(st.integers(0, 2 ** 31 - 1), st.integers(1, 3), st.integers(1, 400), st.sampled_from([8, 32, 100]))
 def test_moving_render_is_the_segment_crossfade(seed, S, L, seg_len):
     # brute force with dense filters and numpy.convolve: in segment j >= 1 the reflection output
