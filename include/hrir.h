@@ -79,8 +79,9 @@ void hrir_destroy(hrir_ctx *ctx);
 const char *hrir_last_error(const hrir_ctx *ctx);
 
 /* Wait for all work enqueued on `stream`, then return and clear any device-side error flag:
- * HRIR_EINVAL (a direction id was out of range, that source rendered as silence, or a
- * device tap table of hrir_render_moving held an invalid entry, which was ignored),
+ * HRIR_EINVAL (a direction id was out of range, that source rendered as silence, a
+ * device tap table of hrir_render_moving held an invalid entry, which was ignored, or an
+ * hrir_sparsify row hit the solver's limits),
  * HRIR_ETIMEDOUT (a bounded wait expired; the output of that call is incomplete), or
  * HRIR_ECUDA if the stream reported a CUDA error. */
 int hrir_sync(hrir_ctx *ctx, void *stream);
@@ -144,7 +145,11 @@ int64_t hrir_out_len(const hrir_ctx *ctx, int64_t len, int full);
  *           columns [0, out_len) are overwritten, the rest untouched.
  *   stream  cudaStream_t to enqueue on.
  * Every source is read once per render; the mix is deterministic (fixed summation order
- * for a given device and shape).  n_src == 0 writes zeros; len == 0 writes nothing.
+ * for a given device and shape).  Accuracy: no FP32 sum in the mix runs over more than a
+ * few hundred products (HRIR_SPARSE: registers folded every ~64 products into per-lane
+ * accumulators, flushed every 64 sources; HRIR_DENSE: runs of 8 sources), the runs'
+ * partial sums are added with compensation (Kahan) and the resonance stage is a
+ * compensated dot product.  n_src == 0 writes zeros; len == 0 writes nothing.
  * ------------------------------------------------------------------------------------- */
 int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hrir_dtype dt,
                       const void *src, const int32_t *dir, hrir_mode mode, int full,
@@ -204,16 +209,21 @@ int hrir_stream_close(hrir_ctx *ctx);
  * The paper has no counterpart to this call; it exists only for those callers.
  *
  * hrir_render_batch keeps its partial sums in a workspace that it grows with cudaMalloc.
- * This call uses instead a fixed 32 MiB array of device memory that every GPU loading the
- * library holds until the process exits; it calls no cudaMalloc, cudaFree or other
- * allocating routine.  Renders whose partial sums need more than 32 MiB (about
- * n_tiles * ceil(n_src / 64 + 2) * 52 KiB, n_tiles = ceil((len + Lg - 1) / 6656) for
- * HRIR_SPARSE) are rejected with HRIR_EINVAL and a message giving the size needed.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture.  Every call
- * shares the one array, so calls whose GPU work overlaps in time (on different streams or
- * from different contexts) race on it: serialize them.  Nothing in the array needs to be
- * cleared between calls.
+ * This call uses instead a fixed 32 MiB array of device memory; it calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Renders whose partial sums need more than 32 MiB
+ * (about n_tiles * (ceil(n_src / 64) + 2) * 52 KiB, n_tiles = ceil((len + Lg - 1) / 6656)
+ * for HRIR_SPARSE; n_tiles * (ceil(n_src / 8) + 2) * 72 KiB, n_tiles = ceil((len + H - 1) /
+ * 9216) for HRIR_DENSE) are rejected with HRIR_EINVAL and a message giving the size needed.
+ * Set-up on first use: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current).  Under CUDA's lazy module loading (the
+ * default) that lookup is also when the driver loads the array and reserves its 32 MiB, so
+ * the first call can block in the driver or fail with HRIR_ENOMEM.  Make one call at set-up
+ * time, before the real-time phase and before any stream capture; from then on the device
+ * holds the array until the process exits and later calls allocate nothing.
+ * Every call shares the one array, so calls whose GPU work overlaps in time (on different
+ * streams or from different contexts) race on it: serialize them.  Nothing in the array
+ * needs to be cleared between calls.  This call's kernels are not timed by hrir_set_timing
+ * (timing would create CUDA events).
  * ------------------------------------------------------------------------------------- */
 int hrir_render_batch_noalloc(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld,
                               hrir_dtype dt, const void *src, const int32_t *dir,
@@ -311,6 +321,51 @@ int hrir_resonance_per_source(hrir_ctx *ctx, int n_src, int64_t len, int64_t src
                               int64_t out_ld, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Filter production on the device (Sec. III): the factorization x = f * g of Eq. 1 from a
+ * set of HRIRs (Algorithm 1) and its sparsifying fine-tune (Eq. 14), so that the tap tables
+ * hrir_load_filters takes can be made from measured HRIRs without leaving the GPU.  Both run
+ * per ear; every array is device memory, row-major, directions outermost:
+ *   X  float [n_dirs][n_ears][M]   the HRIRs (the paper's columns x_i), M = hrir_len = Lf + Lg - 1
+ *   G  float [n_dirs][n_ears][Lg]  reflection filters g_i (rows of the paper's G, >= 0)
+ *   f  float [n_ears][Lf]          the direction-independent resonance filter of each ear
+ * Arithmetic is FP32; the normal equations, residuals and the solvers' residuals are
+ * accumulated in double-float (error-free transformations), so results agree with an FP64
+ * computation to a few FP32 ulps per step.  No FP64 arithmetic runs on the device.
+ * 1 <= n_ears <= 2, 1 <= Lf <= 64.  Workspace comes from the context.
+ *
+ * hrir_factorize  Algorithm 1's alternating minimisation: `iters` rounds of (1) the least-
+ *                 squares resonance for the current G (the normal equations of Eqs. 9-11 over
+ *                 the Lf free parameters of the banded Toeplitz form, Eqs. 12-13, solved by
+ *                 Cholesky with iterative refinement) and (2) the multiplicative non-negative
+ *                 update of G (Eq. 4 with F = F~, the banded Toeplitz matrix of f); entries of
+ *                 G equal to 0 stay 0.  G holds the start on entry (Algorithm 1 draws it
+ *                 uniformly at random: the caller passes it in, >= 0) and the result on return;
+ *                 f receives the resonance of the last round.  trace (may be NULL), float
+ *                 [n_ears][iters + 1]: ||X - F~ G^T||_F^2 after the first solve with the
+ *                 starting G, then after each round's update.  normalise != 0: f is scaled to
+ *                 unit L2 norm and G by the inverse factor at the end (F~ G^T unchanged).
+ *                 1 <= Lg <= 1024, iters >= 1.
+ * hrir_sparsify   The fine-tune of Sec. III-D with f fixed: per direction and ear the
+ *                 L1-regularised non-negative least squares problem
+ *                     g_i = argmin_{g >= 0} ||D (F~ g - x_i)||^2 + lam sum_j g_j     (Eq. 14)
+ *                 with D = I (sigma <= 0) or the window transform D_W = diag(exp(-m^2 /
+ *                 sigma^2)), m = 0..M-1 (Eq. 16), solved exactly by an active-set method; then
+ *                 entries <= thresh are set to 0 (the paper discards those below 1e-4).  G out;
+ *                 nnz (may be NULL), int32 [n_dirs][n_ears]: non-zeros kept per row.  A row
+ *                 whose support would exceed the solver's limit (min(Lg, 128) and the shared
+ *                 memory available) keeps its last feasible iterate and flags HRIR_EINVAL for
+ *                 hrir_sync.  lam >= 0, thresh >= 0.
+ * Tap tables for hrir_load_filters follow from G with hrir_topk_pack (k = the largest nnz
+ * keeps every non-zero: a table of variable NNZE per direction).
+ * ------------------------------------------------------------------------------------- */
+int hrir_factorize(hrir_ctx *ctx, int n_dirs, int n_ears, int hrir_len, int refl_len,
+                   const float *X, float *G, float *f, float *trace, int iters, int normalise,
+                   void *stream);
+int hrir_sparsify(hrir_ctx *ctx, int n_dirs, int n_ears, int hrir_len, int refl_len,
+                  const float *X, const float *f, float lam, float sigma, float thresh, float *G,
+                  int32_t *nnz, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * Optional kernel timing, for benchmarks.  While enabled, the library brackets each of its
  * kernel launches with CUDA events recorded on the launching stream.  hrir_kernel_times
  * waits for those events and writes, per kernel family (hrir_kernel), the accumulated
@@ -326,7 +381,8 @@ typedef enum {
     HRIR_K_MLP = 5,         /* learned-filter network kernels (forward, backward, Adam) */
     HRIR_K_MOVING = 6,      /* moving-source crossfade mixing kernel */
     HRIR_K_RESONANCE = 7,   /* per-source resonance on the tensor cores */
-    HRIR_K_COUNT = 8
+    HRIR_K_FILTERS = 8,     /* filter production (factorization, L1-NNLS) */
+    HRIR_K_COUNT = 9
 } hrir_kernel;
 
 int hrir_set_timing(hrir_ctx *ctx, int enable);

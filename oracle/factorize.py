@@ -119,7 +119,8 @@ def residual(X, f, G) -> float:
 
 
 def factorize(X, refl_len: int, G0, iters: int = 50, normalise: bool = True):
-    """Algorithm 1 without the final fine-tune: for t = 1..T, solve f, form F~, update G.
+    """The alternating minimisation of Algorithm 1 (without its final sparsifying fine-tune):
+    T rounds of a resonance solve with G fixed followed by a reflection update with f fixed.
 
     X: M x N HRIRs (columns).  G0: N x Lg non-negative initialisation.
     Returns (f, G, trace) where trace[t] = residual after iteration t (trace[0] is the
@@ -135,11 +136,15 @@ def factorize(X, refl_len: int, G0, iters: int = 50, normalise: bool = True):
     trace = []
     f = None
     for t in range(iters):
-        f = solve_resonance(X, G, res_len)                       # Theta <- A^-1 b
-        F = toeplitz_filter_matrix(f, refl_len)                  # F~ <- Top(Theta)
+        # the least-squares resonance for the current G: normal equations of Eq. 9-10,
+        # solved as in Eq. 11 over the Lf free parameters of the banded form (Eq. 13)
+        f = solve_resonance(X, G, res_len)
+        # its banded Toeplitz matrix (Eq. 12), the F of the semi-NMF objective (Eq. 3)
+        F = toeplitz_filter_matrix(f, refl_len)
         if t == 0:
             trace.append(residual(X, f, G))
-        G = update_reflections(X, F, G)                          # multiplicative update
+        # non-negative reflections for that F: the sign-split ratio rule of Eq. 4
+        G = update_reflections(X, F, G)
         trace.append(residual(X, f, G))
     if normalise and f is not None:
         s = float(np.linalg.norm(f))

@@ -43,6 +43,8 @@ struct hrir_ctx {
     cudaEvent_t copy_ev[5] = {};        // [chunks]: chunk copied; [chunks]: caller's work before
     void *d_mlp_ws = nullptr;           // learned-filter network workspace
     size_t mlp_ws_bytes = 0;
+    void *d_fact_ws = nullptr;          // filter-production workspace (factorization, L1-NNLS)
+    size_t fact_ws_bytes = 0;
     int *d_status = nullptr;
 
     // optional kernel timing (hrir_set_timing)
@@ -65,8 +67,14 @@ size_t dtype_size(int dt);
 // Make *ptr hold at least `need` bytes of device memory (grown with 1/8 slack).
 int grow(hrir_ctx *ctx, void **ptr, size_t *have, size_t need);
 int64_t round_up(int64_t x, int64_t m);
-// Pipeline depth (2..4) that fits the 227 KB shared-memory limit; 0 if none does.
-int pick_stages(int buf_elems, int elem_bytes, int rec_bytes, size_t *smem);
+// Sources per register accumulation run of the sparse (taps of the loaded tables) or dense
+// mixing kernel; hrir_render_batch and hrir_render_batch_noalloc use the same value.
+int mix_run_sources(const hrir_ctx *ctx, bool sparse);
+// Sources per register fold of the sparse mixing kernel (kFoldTerms / k_max, at least 1).
+int mix_fold_sources(const hrir_ctx *ctx);
+// Pipeline depth (2..kMixMaxStages) that fits the 227 KB shared-memory limit with `extra`
+// bytes after the mixing kernel's own layout (16-byte aligned, at *smem - extra); 0 if none.
+int pick_stages(int buf_elems, int elem_bytes, int rec_bytes, size_t extra, size_t *smem);
 // 2-D tensor map over the sources: dims {len, n_src}, row stride ld, box {kMixBox, 1}.
 int make_source_map(hrir_ctx *ctx, CUtensorMap *m, const void *src, int dt, int64_t len,
                     int64_t ld, int n_src, int box_rows = 1);

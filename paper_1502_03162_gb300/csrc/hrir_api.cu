@@ -53,6 +53,17 @@ int grow(hrir_ctx *ctx, void **ptr, size_t *have, size_t need)
     return HRIR_OK;
 }
 
+int mix_fold_sources(const hrir_ctx *ctx)
+{
+    return std::max(1, kFoldTerms / std::max(ctx->k_max, 1));
+}
+
+int mix_run_sources(const hrir_ctx *ctx, bool sparse)
+{
+    (void)ctx;
+    return sparse ? kRunSources : kDenseRunSources;
+}
+
 void free_tables(hrir_ctx *ctx)
 {
     cudaFree(ctx->d_sparse);
@@ -79,10 +90,10 @@ size_t dtype_size(int dt) { return dt == HRIR_F32 ? 4 : 2; }
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // Pipeline depth that fits the 227 KB shared-memory limit.
-int pick_stages(int buf_elems, int elem_bytes, int rec_bytes, size_t *smem)
+int pick_stages(int buf_elems, int elem_bytes, int rec_bytes, size_t extra, size_t *smem)
 {
     for (int st = kMixMaxStages; st >= 2; --st) {
-        size_t b = mix_smem_bytes(buf_elems, elem_bytes, rec_bytes, st);
+        size_t b = (size_t)round_up((int64_t)mix_smem_bytes(buf_elems, elem_bytes, rec_bytes, st), 16) + extra;
         if (b <= 227 * 1024) {
             *smem = b;
             return st;
@@ -284,6 +295,7 @@ void hrir_destroy(hrir_ctx *ctx)
     cudaFree(ctx->d_partial);
     cudaFree(ctx->d_stage);
     cudaFree(ctx->d_mlp_ws);
+    cudaFree(ctx->d_fact_ws);
     cudaFree(ctx->d_status);
     delete ctx;
 }
@@ -338,6 +350,9 @@ int hrir_sync(hrir_ctx *ctx, void *stream)
         return fail(ctx, HRIR_ETIMEDOUT, "a bounded device wait expired (output incomplete)");
     if (st & DEV_BAD_TAP)
         return fail(ctx, HRIR_EINVAL, "a device tap table held an index >= Lg or a count > k_max (ignored)");
+    if (st & DEV_SOLVER)
+        return fail(ctx, HRIR_EINVAL, "an L1-NNLS row outgrew the solver's support limit or iteration "
+                                      "limit (its result is the last feasible iterate)");
     return fail(ctx, HRIR_EINVAL, "a direction id was out of range (rendered as silence)");
 }
 
@@ -532,7 +547,8 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
     const int64_t mix_len = sparse ? std::min<int64_t>(out_len, len + ctx->refl_len - 1) : out_len;
     const int n_tiles = (int)((mix_len + tile - 1) / tile);
     size_t smem = 0;
-    const int stages = pick_stages(buf_elems, (int)es, rec_bytes, &smem);
+    const size_t extra = sparse ? (size_t)kSparseRunAccBytes : 0;
+    const int stages = pick_stages(buf_elems, (int)es, rec_bytes, extra, &smem);
     if (stages == 0) return fail(ctx, HRIR_EINVAL, "filters too long for the shared-memory pipeline");
     CUtensorMap tmap, tmap3;
     int rc = make_source_map(ctx, &tmap, src, (int)dt, len, src_ld, n_src);
@@ -544,7 +560,7 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
     part.U = (int64_t)n_tiles * n_src;
     part.P = std::min<int64_t>(ctx->num_sms, part.U);
     part.n_src = n_src;
-    part.gs = kRunSources;
+    part.gs = mix_run_sources(ctx, sparse);
     int slots = 0;
     for (int t = 0; t < n_tiles; ++t) slots = std::max(slots, part.slots(t));
     const size_t pbytes = (size_t)n_tiles * slots * 2 * tile * sizeof(float);
@@ -567,6 +583,8 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
     a.full_rows = (int)(len / kMixBox);
     a.n_tiles = n_tiles;
     a.stages = stages;
+    a.runacc_off = (int)(smem - extra);
+    a.fold = mix_fold_sources(ctx);
     a.part = part;
     a.partial = ctx->d_partial;
     a.slots = slots;

@@ -28,6 +28,8 @@ constexpr int kSparseR = 52, kSparseWarps = 21, kSparseQuarters = 4;
 constexpr int kSparseTile = kSparseQuarters * 32 * kSparseR;
 constexpr int kSparseTmemCols = 256;
 constexpr int kSparseSegment = kSparseTmemCols - kSparseR;  // 204
+// per-lane FP32 fold accumulators of the 16 tap warps (26 outputs per lane each)
+constexpr int kSparseRunAccBytes = 16 * 32 * (kSparseR / 2) * 4;
 constexpr int kDenseR = HRIR_DENSE_R, kDenseWarps = HRIR_DENSE_WARPS;
 constexpr int kMixMaxStages = 6;
 constexpr int kMixDirCache = 2048;                // unit directions staged in shared memory
@@ -37,7 +39,27 @@ constexpr int kMixDirCache = 2048;                // unit directions staged in s
 constexpr int kMixWindowBars = 16;
 constexpr int kMixSmemTail = kMixWindowBars * 8 + 16 + 2 * kMixMaxStages * 4 + kMixDirCache * 4;
 constexpr int kMixBox = 256;                      // TMA box width (elements)
-constexpr int kRunSources = 64;                   // max sources per register accumulation run
+constexpr int kRunSources = 64;                   // max sources per partial slot (a run)
+// Accuracy of the FP32 mix.  The rounding error of a sequential FP32 sum of n terms grows as
+// sqrt(n), and the resonance stage, applied after the mix, can magnify the mix's relative
+// error where f attenuates the band that holds the sources' energy.  So every sum is kept
+// short or split in two levels:
+//  * sparse kernel: its tap registers are folded every kFoldTerms products (fold = max(1,
+//    kFoldTerms / K) sources) into a per-lane FP32 accumulator in shared memory, which is
+//    flushed to the run's partial slot every kRunSources sources (sums of ~64 terms at
+//    either level);
+//  * dense kernel (231 products per source): runs of kDenseRunSources sources;
+//  * moving-source kernel (2K products per source): runs of run_sources(2K) sources, at most
+//    kAccumTerms products.
+constexpr int kFoldTerms = 64;
+constexpr int kDenseRunSources = 8;
+constexpr int kAccumTerms = 512;
+// Sources per accumulation run for `terms` products per source and output.
+inline int run_sources(int terms)
+{
+    const int g = kAccumTerms / (terms > 0 ? terms : 1);
+    return g < 1 ? 1 : (g > kRunSources ? kRunSources : g);
+}
 
 enum MixMode : int { MIX_SPARSE = 0, MIX_DENSE = 1 };
 
@@ -58,6 +80,9 @@ struct MixArgs {
     int full_rows;              // floor(len / kMixBox): rows of the 3-D source view
     int n_tiles;
     int stages;                 // pipeline depth (2..kMixMaxStages)
+    int runacc_off;             // sparse: byte offset of the per-lane fold accumulators in
+                                // dynamic shared memory (kSparseRunAccBytes)
+    int fold;                   // sparse: sources per register fold (>= 1)
     Partition part;
     float *partial;             // [n_tiles][slots][2][tile]
     int slots;
@@ -234,6 +259,49 @@ size_t resonance_gemm_smem_bytes(int elem_bytes);
 // tmap: 2-D tensor map over the 16-bit sources with box {256, 1}
 cudaError_t launch_resonance_gemm(int dtype, const CUtensorMap &tmap, const ResonanceArgs &a,
                                   int grid, cudaStream_t st);
+
+// ---- filter production: the alternating minimisation of Algorithm 1 (factorize.cu) --------
+constexpr int kFactMaxLf = 64;   // resonance taps the Toeplitz solve supports
+struct FactArgs {
+    int n_dirs, n_ears, M, Lg, Lf, iters;
+    const float *X;              // [n_dirs][n_ears][M] HRIRs
+    float *G;                    // [n_dirs][n_ears][Lg] reflections (updated in place)
+    const float *f;              // [n_ears][Lf] resonance of the round (round kernel)
+    const float *R;              // [n_ears][Lf] its autocorrelation lags (round kernel)
+    float *f_out;                // [n_ears][Lf] the solved resonance (solve kernel)
+    float *R_out;                // [n_ears][Lf] its autocorrelation lags (solve kernel)
+    float2 *part;                // [n_ears][n_dirs][2 Lf + 2] double-float row partials
+    float *trace;                // [n_ears][iters + 1] residuals, or nullptr
+    float *scale;                // [n_ears] final norms of f
+    int update, res_before, partials;   // set by launch_fact_round
+};
+size_t fact_round_smem_bytes(int M, int Lg, int Lf);
+// one round over every (row, ear): update G (update != 0), residuals, partials of A and b
+cudaError_t launch_fact_round(const FactArgs &a, int update, int res_before, int partials,
+                              cudaStream_t st);
+// per ear: sum the partials; trace entries (index >= 0); solve for f and its lags (solve != 0)
+cudaError_t launch_fact_solve(const FactArgs &a, int solve, int trace_before, int trace_after,
+                              cudaStream_t st);
+// f_e <- f_e / ||f_e||, G_e <- G_e ||f_e||
+cudaError_t launch_fact_normalise(const FactArgs &a, cudaStream_t st);
+
+// ---- filter production: L1-NNLS sparsification, Eq. 14 with D_I or D_W (sparsify.cu) ---------
+struct SparsifyArgs {
+    int n_dirs, n_ears, M, Lg, Lf;
+    int cap;                     // largest support the solver holds (<= Lg)
+    const float *X;              // [n_dirs][n_ears][M] HRIRs
+    const float *f;              // [n_ears][Lf] resonance (fixed)
+    float lam;                   // lambda of Eq. 14
+    float inv_sigma2;            // 1 / sigma^2 of D_W (Eq. 16), 0 for D = I
+    float thresh;                // entries <= thresh are discarded
+    float tol;                   // stop when max w off the support <= tol * max |c|
+    float2 *q;                   // [n_ears][Lg][Lf] workspace: the band of Q (double-float)
+    float *G;                    // [n_dirs][n_ears][Lg] out
+    int32_t *nnz;                // [n_dirs][n_ears] out, or nullptr
+    int *status;                 // DEV_SOLVER when a support outgrew cap or the loop limit
+};
+size_t sparsify_smem_bytes(int M, int Lg, int Lf, int cap);
+cudaError_t launch_sparsify(const SparsifyArgs &a, cudaStream_t st);
 
 // ---- table builders and top-K -------------------------------------------------------------
 cudaError_t launch_topk(const float *g, int n_rows, int refl_len, int k, uint16_t *idx, float *w,

@@ -24,8 +24,11 @@
 // halo, hardware zero fill outside [0, len)) and the direction's tap record (bulk copy); a
 // producer warp issues every load, refilling each stage with the unit `stages` ahead as soon
 // as the 20 compute warps have released it.
-// Work is a persistent balanced range of units per CTA; register accumulators are
-// flushed every <= 64 sources into partial slots that the reduction sums in a fixed order.
+// Work is a persistent balanced range of units per CTA; register accumulators are folded
+// every few sources (about 64 products per output) into per-lane FP32 accumulators in shared
+// memory, which are flushed every <= 64 sources into partial slots that the reduction sums
+// in a fixed order (two short sums instead of one long one: the FP32 rounding error grows
+// with the square root of a sum's length).
 // All waits are bounded: a wait that expires raises the CTA's abort flag, and every other
 // wait then returns at once, so all warps leave their loops.
 #include <cuda_bf16.h>
@@ -450,7 +453,13 @@ __global__ void __maxnreg__(80)
             uint64_t acc[RP];
 #pragma unroll
             for (int i = 0; i < RP; ++i) acc[i] = 0;
-            int slot = a.part.slot_base(blockIdx.x, pos0.t), run_n = 0, toff = 0;
+            // this lane's fold accumulators in shared memory, [RP][32] packed pairs per warp
+            // (a warp's 8-byte accesses are contiguous: conflict-free); only this thread
+            // touches them
+            uint64_t *racc = reinterpret_cast<uint64_t *>(smem + a.runacc_off) + (size_t)warp * RP * 32 + lane;
+#pragma unroll
+            for (int i = 0; i < RP; ++i) racc[i * 32] = 0;
+            int slot = a.part.slot_base(blockIdx.x, pos0.t), run_n = 0, toff = 0, fold_n = 0;
             for (int64_t j = 0; j < n_steps; ++j) {
                 const uint32_t buf = (uint32_t)j & 1u;
                 if (seg == 0 && !mbar_wait_bounded(smem_addr(&bars[st]), ph, abort_flag, a.status))
@@ -470,22 +479,41 @@ __global__ void __maxnreg__(80)
                 toff += c.x + c.y;
                 if (seg == n_seg - 1) {
                     release(st);                              // last read of unit k's stage
-                    // unit k done: flush the run at its end
+                    // unit k done: every `fold` sources the registers are added into the
+                    // shared-memory accumulators; at the end of the run their sum goes to the
+                    // run's partial slot
                     ++run_n;
+                    ++fold_n;
                     const bool tile_end = (k + 1 == n_units) || (pos.s + 1 == a.n_src);
-                    if (run_n == a.part.gs || tile_end) {
-                        float2 *p = reinterpret_cast<float2 *>(a.partial + ((size_t)pos.t * a.slots + slot) * 2 * kTile +
-                                                               ear * kTile + lane_off + RS * half);
+                    const bool flush = run_n == a.part.gs || tile_end;
+                    if (flush || fold_n == a.fold) {
+                        fold_n = 0;
+                        uint64_t one2;
+                        asm("mov.b64 %0, {%1, %1};" : "=l"(one2) : "r"(0x3f800000u));
+                        if (flush) {
+                            float2 *p = reinterpret_cast<float2 *>(a.partial + ((size_t)pos.t * a.slots + slot) * 2 * kTile +
+                                                                   ear * kTile + lane_off + RS * half);
 #pragma unroll
-                        for (int i = 0; i < RP; ++i) {
-                            float x0, x1;
-                            asm("mov.b64 {%0, %1}, %2;" : "=f"(x0), "=f"(x1) : "l"(acc[i]));
-                            p[i] = make_float2(x0, x1);
+                            for (int i = 0; i < RP; ++i) {
+                                uint64_t x = racc[i * 32];
+                                asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(x) : "l"(one2), "l"(acc[i]));
+                                float x0, x1;
+                                asm("mov.b64 {%0, %1}, %2;" : "=f"(x0), "=f"(x1) : "l"(x));
+                                p[i] = make_float2(x0, x1);
+                                racc[i * 32] = 0;
+                            }
+                            ++slot;
+                            run_n = 0;
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < RP; ++i) {
+                                uint64_t x = racc[i * 32];
+                                asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(x) : "l"(one2), "l"(acc[i]));
+                                racc[i * 32] = x;
+                            }
                         }
 #pragma unroll
                         for (int i = 0; i < RP; ++i) acc[i] = 0;
-                        ++slot;
-                        run_n = 0;
                     }
                     toff = 0;
                     pos.advance(1, a.n_src);

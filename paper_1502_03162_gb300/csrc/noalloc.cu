@@ -2,11 +2,13 @@
 // partial-sum scratch held in a fixed, file-scope device array instead of the context's
 // growable workspace, so the call itself allocates nothing.
 //
-// The scratch is kNoAllocScratchBytes (32 MiB) of device memory that every GPU which loads
-// this library keeps until the process exits.  Host code must not pass the array's name to a
-// kernel (on the host it is only a stand-in symbol); its device address is fetched once per
-// device with cudaGetSymbolAddress, with that device current, on the first call made on that
-// device, and cached.
+// The scratch is kNoAllocScratchBytes (32 MiB) of device memory.  This file holds no kernel,
+// so the array sits in a module of its own; under CUDA's lazy module loading (the default)
+// that module is loaded, and its 32 MiB reserved, on the first call made on a device, when
+// the array's address is looked up.  From then on the device keeps the array until the
+// process exits.  Host code must not pass the array's name to a kernel (on the host it is
+// only a stand-in symbol); its device address is fetched once per device with
+// cudaGetSymbolAddress, with that device current, and cached.
 #include <mutex>
 
 #include "api_internal.h"
@@ -33,9 +35,12 @@ int scratch_address(hrir_ctx *ctx, float **out)
     if (!g_scratch_addr[ctx->device]) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
-        if (e != cudaSuccess || !p)
-            return fail(ctx, HRIR_ECUDA, "cudaGetSymbolAddress of the fixed scratch failed: %s",
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();   // do not leave the error for the next launch check to report
+            return fail(ctx, e == cudaErrorMemoryAllocation ? HRIR_ENOMEM : HRIR_ECUDA,
+                        "cudaGetSymbolAddress of the fixed scratch failed: %s",
                         cudaGetErrorString(e));
+        }
         g_scratch_addr[ctx->device] = static_cast<float *>(p);
     }
     *out = g_scratch_addr[ctx->device];
@@ -91,7 +96,7 @@ extern "C" int hrir_render_batch_noalloc(hrir_ctx *ctx, int n_src, int64_t len, 
     part.U = (int64_t)n_tiles * n_src;
     part.P = std::min<int64_t>(ctx->num_sms, part.U);
     part.n_src = n_src;
-    part.gs = kRunSources;
+    part.gs = mix_run_sources(ctx, sparse);
     int slots = 0;
     for (int t = 0; t < n_tiles; ++t) slots = std::max(slots, part.slots(t));
     const size_t need = (size_t)n_tiles * slots * 2 * tile * sizeof(float);
@@ -103,7 +108,8 @@ extern "C" int hrir_render_batch_noalloc(hrir_ctx *ctx, int n_src, int64_t len, 
                     need, kNoAllocScratchBytes);
 
     size_t smem = 0;
-    const int stages = pick_stages(buf_elems, (int)es, rec_bytes, &smem);
+    const size_t extra = sparse ? (size_t)kSparseRunAccBytes : 0;
+    const int stages = pick_stages(buf_elems, (int)es, rec_bytes, extra, &smem);
     if (stages == 0) return fail(ctx, HRIR_EINVAL, "filters too long for the shared-memory pipeline");
     CUtensorMap tmap, tmap3;
     rc = make_source_map(ctx, &tmap, src, (int)dt, len, src_ld, n_src);
@@ -129,6 +135,8 @@ extern "C" int hrir_render_batch_noalloc(hrir_ctx *ctx, int n_src, int64_t len, 
     a.full_rows = (int)(len / kMixBox);
     a.n_tiles = n_tiles;
     a.stages = stages;
+    a.runacc_off = (int)(smem - extra);
+    a.fold = mix_fold_sources(ctx);
     a.part = part;
     a.partial = scratch;
     a.slots = slots;

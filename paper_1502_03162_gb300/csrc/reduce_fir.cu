@@ -2,7 +2,8 @@
 //
 //   z_e[m]   = sum over the partial slots of tile(m), in slot order, compensated (Kahan)
 //   out_e[n] = sum_{l < Lf} f_e[l] z_e[n - l]          (the resonance stage of Eq. 2;
-//                                                      identity when no filter is given)
+//                                                      identity when no filter is given),
+//              a compensated dot product
 // Each block produces kBlk outputs of one ear: it first forms z for [n0 - Lf + 1, n0 + kBlk)
 // in shared memory (coalesced partial reads, fixed summation order), then applies the FIR.
 #include "kernels.h"
@@ -54,9 +55,23 @@ __global__ void __launch_bounds__(kThreads) reduce_fir_kernel(const ReduceArgs a
     for (int i = threadIdx.x; i < kBlk; i += kThreads) {
         const int64_t n = n0 + i;
         if (n >= a.out_len) break;
-        float acc = 0.f;
-        for (int l = 0; l < lf; ++l) acc = fmaf(fs[l], zs[i + lf - 1 - l], acc);
-        a.out[e * a.out_ld + n] = acc;
+        // compensated dot product (Ogita, Rump & Oishi 2005, "Dot2"): the products' and the
+        // running sum's rounding errors are carried exactly (error-free transformations)
+        // and added at the end, so the result is as accurate as a sum in twice the working
+        // precision; the FIR can cancel most of z where f attenuates z's band, which would
+        // otherwise magnify its FP32 rounding relative to the output
+        float p = 0.f, c = 0.f;
+        for (int l = 0; l < lf; ++l) {
+            const float x = fs[l], y = zs[i + lf - 1 - l];
+            const float h = __fmul_rn(x, y);
+            const float r = fmaf(x, y, -h);               // h + r == x * y exactly
+            const float s2 = __fadd_rn(p, h);
+            const float bb = __fsub_rn(s2, p);
+            const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(s2, bb)), __fsub_rn(h, bb));  // p + h == s2 + q
+            p = s2;
+            c = __fadd_rn(c, __fadd_rn(q, r));
+        }
+        a.out[e * a.out_ld + n] = __fadd_rn(p, c);
     }
 }
 
