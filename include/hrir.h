@@ -168,8 +168,9 @@ int hrir_render_batch_host(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld
                            int full, float *out, int64_t out_ld, void *stream);
 
 /* ---------------------------------------------------------------------------------------
- * Block streaming with continuous batching: partitioned time-domain convolution, which
- * "incurs neither memory overhead nor latency" (Sec. IV-G), on the filters of Eqs. 1-2.
+ * Block streaming with continuous batching: partitioned time-domain convolution, which adds
+ * no latency and needs no extra memory when split into blocks (Sec. IV-G), on the filters
+ * of Eqs. 1-2.
  *
  * hrir_stream_open  Opens the context's stream: blocks of `block` (128 or 256) samples, at most
  *                   max_slots sources at once, a device pool of pool_bytes for source samples;
@@ -321,46 +322,28 @@ int hrir_resonance_per_source(hrir_ctx *ctx, int n_src, int64_t len, int64_t src
                               int64_t out_ld, void *stream);
 
 /* ---------------------------------------------------------------------------------------
- * Filter production on the device (Sec. III): the factorization x = f * g of Eq. 1 from a
- * set of HRIRs (Algorithm 1) and its sparsifying fine-tune (Eq. 14), so that the tap tables
- * hrir_load_filters takes can be made from measured HRIRs without leaving the GPU.  Both run
- * per ear; every array is device memory, row-major, directions outermost:
- *   X  float [n_dirs][n_ears][M]   the HRIRs (the paper's columns x_i), M = hrir_len = Lf + Lg - 1
- *   G  float [n_dirs][n_ears][Lg]  reflection filters g_i (rows of the paper's G, >= 0)
- *   f  float [n_ears][Lf]          the direction-independent resonance filter of each ear
- * Arithmetic is FP32; the normal equations, residuals and the solvers' residuals are
- * accumulated in double-float (error-free transformations), so results agree with an FP64
- * computation to a few FP32 ulps per step.  No FP64 arithmetic runs on the device.
- * 1 <= n_ears <= 2, 1 <= Lf <= 64.  Workspace comes from the context.
- *
- * hrir_factorize  Algorithm 1's alternating minimisation: `iters` rounds of (1) the least-
- *                 squares resonance for the current G (the normal equations of Eqs. 9-11 over
- *                 the Lf free parameters of the banded Toeplitz form, Eqs. 12-13, solved by
- *                 Cholesky with iterative refinement) and (2) the multiplicative non-negative
- *                 update of G (Eq. 4 with F = F~, the banded Toeplitz matrix of f); entries of
- *                 G equal to 0 stay 0.  G holds the start on entry (Algorithm 1 draws it
- *                 uniformly at random: the caller passes it in, >= 0) and the result on return;
- *                 f receives the resonance of the last round.  trace (may be NULL), float
- *                 [n_ears][iters + 1]: ||X - F~ G^T||_F^2 after the first solve with the
- *                 starting G, then after each round's update.  normalise != 0: f is scaled to
- *                 unit L2 norm and G by the inverse factor at the end (F~ G^T unchanged).
- *                 1 <= Lg <= 1024, iters >= 1.
- * hrir_sparsify   The fine-tune of Sec. III-D with f fixed: per direction and ear the
- *                 L1-regularised non-negative least squares problem
- *                     g_i = argmin_{g >= 0} ||D (F~ g - x_i)||^2 + lam sum_j g_j     (Eq. 14)
- *                 with D = I (sigma <= 0) or the window transform D_W = diag(exp(-m^2 /
- *                 sigma^2)), m = 0..M-1 (Eq. 16), solved exactly by an active-set method; then
- *                 entries <= thresh are set to 0 (the paper discards those below 1e-4).  G out;
- *                 nnz (may be NULL), int32 [n_dirs][n_ears]: non-zeros kept per row.  A row
- *                 whose support would exceed the solver's limit (min(Lg, 128) and the shared
- *                 memory available) keeps its last feasible iterate and flags HRIR_EINVAL for
- *                 hrir_sync.  lam >= 0, thresh >= 0.
- * Tap tables for hrir_load_filters follow from G with hrir_topk_pack (k = the largest nnz
- * keeps every non-zero: a table of variable NNZE per direction).
+ * Filter production on the device: the sparsifying fine-tune of Algorithm 1 (Sec. III-D),
+ * so that variable-NNZE tap tables for hrir_load_filters can be made from HRIRs and their
+ * factorized resonance without leaving the GPU.  Per direction and ear, with the
+ * resonance f fixed (F~ = its banded Toeplitz matrix, Eq. 12):
+ *     g_i = argmin_{g >= 0} ||D (F~ g - x_i)||^2 + lam sum_j g_j                   (Eq. 14)
+ * with D = I (sigma <= 0) or the window transform D_W = diag(exp(-m^2 / sigma^2)),
+ * m = 0..M-1 (Eq. 16), solved exactly by an active-set method (Lawson & Hanson's scheme on
+ * the normal-equation form); then entries <= thresh are set to 0 (the paper discards those
+ * below 1e-4).  All arrays are device memory, row-major, directions outermost:
+ *   X    float [n_dirs][n_ears][M]   the HRIRs, M = hrir_len = Lf + Lg - 1
+ *   f    float [n_ears][Lf]          the resonance of each ear (1 <= Lf <= 64)
+ *   G    float [n_dirs][n_ears][Lg]  out: the sparse non-negative reflection filters
+ *   nnz  int32 [n_dirs][n_ears]      out (may be NULL): non-zeros kept per row
+ * FP32 arithmetic; Q = F~^T D^2 F~, c = F~^T D^2 x - lam/2 and every residual are formed in
+ * double-float (error-free transformations) and the support systems are solved by FP32
+ * Cholesky with iterative refinement, so the result agrees with an FP64 solution to FP32
+ * accuracy (no FP64 arithmetic on the device).  A row whose support would exceed the
+ * solver's limit (min(Lg, 128), less if shared memory is short) or whose solve runs over
+ * 1 s keeps its last feasible iterate and flags HRIR_EINVAL for hrir_sync.
+ * 1 <= n_ears <= 2, lam >= 0, thresh >= 0; workspace from the context.  Tap tables follow
+ * from G with hrir_topk_pack (k = the largest nnz keeps every non-zero).
  * ------------------------------------------------------------------------------------- */
-int hrir_factorize(hrir_ctx *ctx, int n_dirs, int n_ears, int hrir_len, int refl_len,
-                   const float *X, float *G, float *f, float *trace, int iters, int normalise,
-                   void *stream);
 int hrir_sparsify(hrir_ctx *ctx, int n_dirs, int n_ears, int hrir_len, int refl_len,
                   const float *X, const float *f, float lam, float sigma, float thresh, float *G,
                   int32_t *nnz, void *stream);
@@ -381,7 +364,7 @@ typedef enum {
     HRIR_K_MLP = 5,         /* learned-filter network kernels (forward, backward, Adam) */
     HRIR_K_MOVING = 6,      /* moving-source crossfade mixing kernel */
     HRIR_K_RESONANCE = 7,   /* per-source resonance on the tensor cores */
-    HRIR_K_FILTERS = 8,     /* filter production (factorization, L1-NNLS) */
+    HRIR_K_FILTERS = 8,     /* filter production (L1-NNLS fine-tune) */
     HRIR_K_COUNT = 9
 } hrir_kernel;
 

@@ -43,7 +43,7 @@ struct hrir_ctx {
     cudaEvent_t copy_ev[5] = {};        // [chunks]: chunk copied; [chunks]: caller's work before
     void *d_mlp_ws = nullptr;           // learned-filter network workspace
     size_t mlp_ws_bytes = 0;
-    void *d_fact_ws = nullptr;          // filter-production workspace (factorization, L1-NNLS)
+    void *d_fact_ws = nullptr;          // filter-production workspace (L1-NNLS fine-tune)
     size_t fact_ws_bytes = 0;
     int *d_status = nullptr;
 

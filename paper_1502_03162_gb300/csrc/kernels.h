@@ -260,34 +260,10 @@ size_t resonance_gemm_smem_bytes(int elem_bytes);
 cudaError_t launch_resonance_gemm(int dtype, const CUtensorMap &tmap, const ResonanceArgs &a,
                                   int grid, cudaStream_t st);
 
-// ---- filter production: the alternating minimisation of Algorithm 1 (factorize.cu) --------
-constexpr int kFactMaxLf = 64;   // resonance taps the Toeplitz solve supports
-struct FactArgs {
-    int n_dirs, n_ears, M, Lg, Lf, iters;
-    const float *X;              // [n_dirs][n_ears][M] HRIRs
-    float *G;                    // [n_dirs][n_ears][Lg] reflections (updated in place)
-    const float *f;              // [n_ears][Lf] resonance of the round (round kernel)
-    const float *R;              // [n_ears][Lf] its autocorrelation lags (round kernel)
-    float *f_out;                // [n_ears][Lf] the solved resonance (solve kernel)
-    float *R_out;                // [n_ears][Lf] its autocorrelation lags (solve kernel)
-    float2 *part;                // [n_ears][n_dirs][2 Lf + 2] double-float row partials
-    float *trace;                // [n_ears][iters + 1] residuals, or nullptr
-    float *scale;                // [n_ears] final norms of f
-    int update, res_before, partials;   // set by launch_fact_round
-};
-size_t fact_round_smem_bytes(int M, int Lg, int Lf);
-// one round over every (row, ear): update G (update != 0), residuals, partials of A and b
-cudaError_t launch_fact_round(const FactArgs &a, int update, int res_before, int partials,
-                              cudaStream_t st);
-// per ear: sum the partials; trace entries (index >= 0); solve for f and its lags (solve != 0)
-cudaError_t launch_fact_solve(const FactArgs &a, int solve, int trace_before, int trace_after,
-                              cudaStream_t st);
-// f_e <- f_e / ||f_e||, G_e <- G_e ||f_e||
-cudaError_t launch_fact_normalise(const FactArgs &a, cudaStream_t st);
-
 // ---- filter production: L1-NNLS sparsification, Eq. 14 with D_I or D_W (sparsify.cu) ---------
+constexpr int kSparsifyMaxLf = 64;   // resonance taps of the fixed f
 struct SparsifyArgs {
-    int n_dirs, n_ears, M, Lg, Lf;
+    int n_dirs, n_ears, M, Lg, Lf;  // Lf <= kSparsifyMaxLf
     int cap;                     // largest support the solver holds (<= Lg)
     const float *X;              // [n_dirs][n_ears][M] HRIRs
     const float *f;              // [n_ears][Lf] resonance (fixed)
@@ -295,7 +271,8 @@ struct SparsifyArgs {
     float inv_sigma2;            // 1 / sigma^2 of D_W (Eq. 16), 0 for D = I
     float thresh;                // entries <= thresh are discarded
     float tol;                   // stop when max w off the support <= tol * max |c|
-    float2 *q;                   // [n_ears][Lg][Lf] workspace: the band of Q (double-float)
+    float *q;                    // 2 planes (leading, trailing parts) of [n_ears][Lg][Lf]:
+                                 // the band of Q in double-float (workspace)
     float *G;                    // [n_dirs][n_ears][Lg] out
     int32_t *nnz;                // [n_dirs][n_ears] out, or nullptr
     int *status;                 // DEV_SOLVER when a support outgrew cap or the loop limit

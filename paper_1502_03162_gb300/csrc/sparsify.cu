@@ -37,12 +37,15 @@ __device__ __forceinline__ float window_sq(int m, float inv_sigma2)
     return inv_sigma2 > 0.f ? expf(-2.f * (float)m * (float)m * inv_sigma2) : 1.f;
 }
 
-// Q band: q[e][j][d] = Q[j][j + d] = sum_m d_m^2 f[m - j] f[m - j - d], d < Lf (double-float)
+// Q band: q[e][j][d] = Q[j][j + d] = sum_m d_m^2 f[m - j] f[m - j - d], d < Lf, as two
+// planes (leading parts, then trailing parts) of a double-float value
 __global__ void sparsify_q_kernel(const SparsifyArgs a)
 {
     const int e = blockIdx.y;
     const int n = a.Lg * a.Lf;
     const float *f = a.f + (size_t)e * a.Lf;
+    float *q_hi = a.q + (size_t)e * n;
+    float *q_lo = a.q + (size_t)a.n_ears * n + (size_t)e * n;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int j = k / a.Lf, d = k - j * a.Lf;
         dfl acc = df_make(0.f);
@@ -54,13 +57,16 @@ __global__ void sparsify_q_kernel(const SparsifyArgs a)
                 acc = df_fma_df(acc, wf, f[m - j - d]);
             }
         }
-        reinterpret_cast<dfl *>(a.q)[(size_t)e * n + k] = acc;
+        q_hi[k] = acc.hi;
+        q_lo[k] = acc.lo;
     }
 }
 
 struct Smem {
-    dfl *q;       // [Lg][Lf] band of Q
-    dfl *c;       // [Lg]
+    float *q_hi;  // [Lg][Lf] band of Q, leading parts
+    float *q_lo;  // [Lg][Lf] trailing parts
+    float *c_hi;  // [Lg] c, leading parts
+    float *c_lo;  // [Lg] trailing parts
     float *g;     // [Lg] current iterate
     float *s;     // [Lg] support solution (entries on P)
     float *xw;    // [M] d^2 x
@@ -76,7 +82,66 @@ __device__ __forceinline__ dfl q_at(const Smem &S, int Lf, int j, int k)
 {
     const int d = k > j ? k - j : j - k;
     if (d >= Lf) return df_make(0.f);
-    return S.q[(j < k ? j : k) * Lf + d];
+    const int o = (j < k ? j : k) * Lf + d;
+    return dfl{S.q_hi[o], S.q_lo[o]};
+}
+
+// Solve Q_PP s_P = c_P on the support P (np = |P|; all threads of the CTA call it): FP32
+// Cholesky of Q_PP, then iterative refinement against the double-float system.  Writes s on P.
+__device__ void solve_support(const Smem &S, int np, int Lf, int Lg, int cap)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int k = 0; k < np; ++k) {
+        for (int r = k + tid; r < np; r += kThreads) {
+            float v = q_at(S, Lf, S.P[r], S.P[k]).hi;
+            for (int p = 0; p < k; ++p) v = fmaf(-S.L[r * (cap + 1) + p], S.L[k * (cap + 1) + p], v);
+            S.rhs[r] = v;     // column k below (and at) the diagonal, before scaling
+        }
+        __syncthreads();
+        if (tid == 0) S.L[k * (cap + 1) + k] = sqrtf(fmaxf(S.rhs[k], 1e-30f));
+        __syncthreads();
+        for (int r = k + 1 + tid; r < np; r += kThreads) S.L[r * (cap + 1) + k] = S.rhs[r] / S.L[k * (cap + 1) + k];
+        __syncthreads();
+    }
+    for (int r = tid; r < np; r += kThreads) {
+        S.s[S.P[r]] = 0.f;
+        S.rhs[r] = __fadd_rn(S.c_hi[S.P[r]], S.c_lo[S.P[r]]);
+    }
+    __syncthreads();
+    for (int it = 0; it <= kRefine; ++it) {
+        if (warp == 0) {
+            // L y = rhs, then L^T z = y (one warp: lanes split each row's dot product)
+            for (int r = 0; r < np; ++r) {
+                float v = 0.f;
+                for (int p = lane; p < r; p += 32) v = fmaf(S.L[r * (cap + 1) + p], S.z[p], v);
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) S.z[r] = (S.rhs[r] - v) / S.L[r * (cap + 1) + r];
+                __syncwarp();
+            }
+            for (int r = np - 1; r >= 0; --r) {
+                float v = 0.f;
+                for (int p = r + 1 + lane; p < np; p += 32) v = fmaf(S.L[p * (cap + 1) + r], S.z[p], v);
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) S.z[r] = (S.z[r] - v) / S.L[r * (cap + 1) + r];
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int r = tid; r < np; r += kThreads) S.s[S.P[r]] += S.z[r];
+        __syncthreads();
+        if (it == kRefine) break;
+        // rhs = c_P - Q_PP s_P (double-float)
+        for (int r = tid; r < np; r += kThreads) {
+            const int jr = S.P[r];
+            dfl acc = {S.c_hi[jr], S.c_lo[jr]};
+            const int k0 = jr - (Lf - 1) > 0 ? jr - (Lf - 1) : 0;
+            const int k1 = jr + (Lf - 1) < Lg - 1 ? jr + (Lf - 1) : Lg - 1;
+            for (int k = k0; k <= k1; ++k)
+                if (S.inP[k]) acc = df_fma_df(acc, df_neg(q_at(S, Lf, jr, k)), S.s[k]);
+            S.rhs[r] = df_value(acc);
+        }
+        __syncthreads();
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) sparsify_kernel(const SparsifyArgs a)
@@ -91,10 +156,14 @@ __global__ void __launch_bounds__(kThreads) sparsify_kernel(const SparsifyArgs a
     Smem S;
     {
         unsigned char *p = smraw;
-        S.q = reinterpret_cast<dfl *>(p);
-        p += sizeof(dfl) * (size_t)Lg * Lf;
-        S.c = reinterpret_cast<dfl *>(p);
-        p += sizeof(dfl) * (size_t)Lg;
+        S.q_hi = reinterpret_cast<float *>(p);
+        p += 4 * (size_t)Lg * Lf;
+        S.q_lo = reinterpret_cast<float *>(p);
+        p += 4 * (size_t)Lg * Lf;
+        S.c_hi = reinterpret_cast<float *>(p);
+        p += 4 * (size_t)Lg;
+        S.c_lo = reinterpret_cast<float *>(p);
+        p += 4 * (size_t)Lg;
         S.g = reinterpret_cast<float *>(p);
         p += 4 * (size_t)Lg;
         S.s = reinterpret_cast<float *>(p);
@@ -115,8 +184,12 @@ __global__ void __launch_bounds__(kThreads) sparsify_kernel(const SparsifyArgs a
     const size_t row = (size_t)i * a.n_ears + e;
     const float *x = a.X + row * M;
     const float *f = a.f + (size_t)e * Lf;
-    const dfl *qg = reinterpret_cast<const dfl *>(a.q) + (size_t)e * Lg * Lf;
-    for (int k = tid; k < Lg * Lf; k += kThreads) S.q[k] = qg[k];
+    const float *qg_hi = a.q + (size_t)e * Lg * Lf;
+    const float *qg_lo = a.q + (size_t)a.n_ears * Lg * Lf + (size_t)e * Lg * Lf;
+    for (int k = tid; k < Lg * Lf; k += kThreads) {
+        S.q_hi[k] = qg_hi[k];
+        S.q_lo[k] = qg_lo[k];
+    }
     for (int m = tid; m < M; m += kThreads) S.xw[m] = x[m];
     for (int j = tid; j < Lg; j += kThreads) {
         S.g[j] = 0.f;
@@ -137,77 +210,25 @@ __global__ void __launch_bounds__(kThreads) sparsify_kernel(const SparsifyArgs a
             const dfl wx = {p, fmaf(w, S.xw[j + l], -p)};
             acc = df_fma_df(acc, wx, f[l]);
         }
-        S.c[j] = df_add(acc, df_make(-0.5f * a.lam));
+        const dfl cj = df_add(acc, df_make(-0.5f * a.lam));
+        S.c_hi[j] = cj.hi;
+        S.c_lo[j] = cj.lo;
     }
     __syncthreads();
     float cmax = 0.f;
-    for (int j = 0; j < Lg; ++j) cmax = fmaxf(cmax, fabsf(S.c[j].hi));
+    for (int j = 0; j < Lg; ++j) cmax = fmaxf(cmax, fabsf(S.c_hi[j]));
     const float tol = a.tol * cmax;
-
-    // solve Q_PP s_P = c_P (np = |P|): FP32 Cholesky, refined against the double-float system
-    auto solve_support = [&](int np) {
-        for (int k = 0; k < np; ++k) {
-            for (int r = k + tid; r < np; r += kThreads) {
-                float v = q_at(S, Lf, S.P[r], S.P[k]).hi;
-                for (int p = 0; p < k; ++p) v = fmaf(-S.L[r * (cap + 1) + p], S.L[k * (cap + 1) + p], v);
-                S.rhs[r] = v;     // column k below (and at) the diagonal, before scaling
-            }
-            __syncthreads();
-            if (tid == 0) S.L[k * (cap + 1) + k] = sqrtf(fmaxf(S.rhs[k], 1e-30f));
-            __syncthreads();
-            for (int r = k + 1 + tid; r < np; r += kThreads) S.L[r * (cap + 1) + k] = S.rhs[r] / S.L[k * (cap + 1) + k];
-            __syncthreads();
-        }
-        for (int r = tid; r < np; r += kThreads) {
-            S.s[S.P[r]] = 0.f;
-            S.rhs[r] = df_value(S.c[S.P[r]]);
-        }
-        __syncthreads();
-        for (int it = 0; it <= kRefine; ++it) {
-            if (warp == 0) {
-                // L y = rhs, then L^T z = y (one warp: lanes split each row's dot product)
-                for (int r = 0; r < np; ++r) {
-                    float v = 0.f;
-                    for (int p = lane; p < r; p += 32) v = fmaf(S.L[r * (cap + 1) + p], S.z[p], v);
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0) S.z[r] = (S.rhs[r] - v) / S.L[r * (cap + 1) + r];
-                    __syncwarp();
-                }
-                for (int r = np - 1; r >= 0; --r) {
-                    float v = 0.f;
-                    for (int p = r + 1 + lane; p < np; p += 32) v = fmaf(S.L[p * (cap + 1) + r], S.z[p], v);
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0) S.z[r] = (S.z[r] - v) / S.L[r * (cap + 1) + r];
-                    __syncwarp();
-                }
-            }
-            __syncthreads();
-            for (int r = tid; r < np; r += kThreads) S.s[S.P[r]] += S.z[r];
-            __syncthreads();
-            if (it == kRefine) break;
-            // rhs = c_P - Q_PP s_P (double-float)
-            for (int r = tid; r < np; r += kThreads) {
-                const int jr = S.P[r];
-                dfl acc = S.c[jr];
-                const int k0 = jr - (Lf - 1) > 0 ? jr - (Lf - 1) : 0;
-                const int k1 = jr + (Lf - 1) < Lg - 1 ? jr + (Lf - 1) : Lg - 1;
-                for (int k = k0; k <= k1; ++k)
-                    if (S.inP[k]) acc = df_fma_df(acc, df_neg(q_at(S, Lf, jr, k)), S.s[k]);
-                S.rhs[r] = df_value(acc);
-            }
-            __syncthreads();
-        }
-    };
 
     int outer = 0;
     const int max_outer = 4 * Lg + 8;
+    const uint64_t t_start = global_timer_ns();
     while (true) {
         // w = c - Q g; the largest w_j off the support (ties: the smaller index)
         float best = -1.f;
         int best_j = -1;
         for (int j = tid; j < Lg; j += kThreads) {
             if (S.inP[j]) continue;
-            dfl acc = S.c[j];
+            dfl acc = {S.c_hi[j], S.c_lo[j]};
             const int k0 = j - (Lf - 1) > 0 ? j - (Lf - 1) : 0;
             const int k1 = j + (Lf - 1) < Lg - 1 ? j + (Lf - 1) : Lg - 1;
             for (int k = k0; k <= k1; ++k)
@@ -241,6 +262,10 @@ __global__ void __launch_bounds__(kThreads) sparsify_kernel(const SparsifyArgs a
                 }
             s_arg = (bj >= 0 && bv > tol && s_np < cap) ? bj : -1;
             if (bj >= 0 && bv > tol && s_np >= cap) s_flag = 1;    // support larger than the cap
+            if (s_arg >= 0 && global_timer_ns() - t_start > kWaitLimitNs) {
+                s_arg = -1;                                         // time budget spent
+                s_flag = 1;
+            }
             if (s_arg >= 0) {
                 S.P[s_np] = s_arg;
                 S.inP[s_arg] = 1;
@@ -252,7 +277,7 @@ __global__ void __launch_bounds__(kThreads) sparsify_kernel(const SparsifyArgs a
         // inner loop: keep the solution on P feasible
         for (int inner = 0; inner <= cap; ++inner) {
             const int np = s_np;
-            solve_support(np);
+            solve_support(S, np, Lf, Lg, cap);
             if (tid == 0) {
                 float alpha = 2.f;
                 int arg = -1;

@@ -1,6 +1,6 @@
 // stream.cu -- block streaming with continuous batching (partitioned time-domain
-// convolution, Sec. IV-G: "neither memory overhead nor latency"), on the factorized filters of
-// Eqs. 1-2.
+// convolution: Sec. IV-G notes that direct convolution split into blocks adds no latency and
+// needs no extra memory), on the factorized filters of Eqs. 1-2.
 //
 // Requests (one source each) are admitted into slots while a device pool has room; their
 // samples are uploaded on a copy stream that overlaps the rendering, and a source admitted
