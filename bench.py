@@ -411,6 +411,49 @@ def bench_learned(rend, torch, seed=13, S=4096, L=96000, seg=256, k=16, train_st
                            "fp32_tflops": 3 * flops_fwd_row * B / (t_train / 1e3) / 1e12}}
 
 
+def bench_sparsified(rend, torch, src, dirs, L, steps, pk, pk_kind):
+    """Variable-NNZE tables from the device's L1-NNLS fine-tune (Eq. 14) of synthetic HRIR set
+    4 (1250 directions x 2 ears) with the set's own resonance, at the paper's lambda = 1e-3,
+    with D = I and with the window transform D_W (sigma = 60 samples, Eq. 16); each table
+    keeps every non-zero (top-K with K = the largest NNZE).  The batch is rendered with them:
+    throughput per mean NNZE of the sources' directions."""
+    from paper_1502_03162_gb300 import hrir, synth
+    X, _, _, p = synth.hrir_set(4)
+    f = (p["res"] / np.linalg.norm(p["res"], axis=1, keepdims=True)).astype(np.float32)
+    Xd = torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda()
+    fd = torch.from_numpy(f).cuda()
+    S = src.shape[0]
+    units = S * L * 2
+    out = torch.empty((2, L + 230), dtype=torch.float32, device="cuda")
+    nb = lambda: None  # noqa: E731
+    dirs_h = dirs.cpu().numpy()
+    res = {}
+    for name, lam, sigma in (("lam1e-3_DI", 1e-3, 0.0), ("lam1e-3_DW60", 1e-3, 60.0)):
+        G = torch.empty((X.shape[0], 2, 200), dtype=torch.float32, device="cuda")
+        nnz = torch.empty((X.shape[0], 2), dtype=torch.int32, device="cuda")
+        fine = lambda: hrir.hrir_sparsify(rend.ctx, Xd, fd, 200, lam, sigma, 1e-4, G=G, nnz=nnz)  # noqa: E731,B023
+        t_fine = time_steps(fine, 2, 1, torch, nb)
+        k = int(nnz.max().item())
+        idx, w, nn = rend.topk_pack(G, k)
+        idx_h = (idx.cpu().numpy().astype(np.int64) & 0xFFFF).astype(np.uint16)
+        nn_h = nn.cpu().numpy()
+        rend.load_filters(idx_h, w.cpu().numpy(), nn_h, 200, f)
+        rend.set_timing(True)
+        rend.kernel_times(reset=True)
+        t = time_steps(lambda: rend.render(src, dirs, mode="sparse", length=L, out=out), steps, 2,
+                       torch, nb)
+        kt = rend.kernel_times(reset=True)
+        rend.set_timing(False)
+        assert rend.sync() == 0
+        nnze = float(nn_h[dirs_h].mean())          # taps per source-ear sample, this batch
+        kms = kt["mix_sparse"][0] / max(kt["mix_sparse"][1], 1)
+        roof = roofline_of(2.0 * nnze * units, S * L * 4.0, kms, pk, pk_kind)
+        res[name] = {"value": units / (t / 1e3), "unit": "source-ear samples/s", "ms_per_step": t,
+                     "mean_nnze": nnze, "max_nnze": k, "fine_tune_ms": t_fine,
+                     "fine_tune_rows": int(X.shape[0] * 2), "roofline": roof}
+    return res
+
+
 def bench_precision(rend, torch, src, dirs, L, steps):
     """BF16/FP16 source storage: the sparse mix (FP32 arithmetic) and the per-source resonance
     on the tensor cores (Toeplitz-block GEMM, y * f for every source and ear)."""
@@ -440,6 +483,20 @@ def bench_precision(rend, torch, src, dirs, L, steps):
                 "kernel_ms": kms, "hbm_gbs": bytes_alg / (kms / 1e3) / 1e9,
                 "tensor_tflops": 768.0 * S * L / (kms / 1e3) / 1e12,
                 "useful_tflops": 128.0 * S * L / (kms / 1e3) / 1e12}
+            # the order (y * f) * g: u rendered to 1 and 4 direction sets by the taps alone
+            rng = np.random.default_rng(21)
+            dsets = torch.from_numpy(np.stack([rng.integers(0, 1250, S).astype(np.int32)
+                                               for _ in range(4)])).cuda()
+            dsets[0].copy_(dirs)
+            vout = torch.empty((4, 2, L + 230), dtype=torch.float32, device="cuda")
+            views = {}
+            for nv in (1, 4):
+                t = time_steps(lambda: hrir.hrir_render_precomputed(rend.ctx, u, dsets[:nv], length=L + 31,  # noqa: B023
+                                                                     out=vout[:nv]),
+                               max(3, steps // 3), 1, torch, nb)
+                views[f"views{nv}"] = {"ms": t, "ms_per_view": t / nv,
+                                       "value": nv * units / (t / 1e3), "unit": "source-ear samples/s"}
+            res["precomputed_views_bf16"] = views
             del u
         del s16
     assert rend.sync() == 0
@@ -647,6 +704,8 @@ def main():
                      "host_link_gbs": h2d / (e2e_ms / 1e3) / 1e9}
 
     if not args.no_extras:
+        result["sparsified"] = bench_sparsified(rend, torch, src, dirs, L, max(3, args.steps // 5),
+                                                pk, pk_kind)
         load(K_DEFAULT)
         result["precision"] = bench_precision(rend, torch, src, dirs, L, max(3, args.steps // 5))
         result["learned"] = bench_learned(rend, torch, S=args.learned_sources)

@@ -349,6 +349,28 @@ int hrir_sparsify(hrir_ctx *ctx, int n_dirs, int n_ears, int hrir_len, int refl_
                   int32_t *nnz, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Rendering precomputed resonance outputs to several direction sets: the order (y * f) * g of
+ * Eq. 2.  Given u_{s,e} = y_s * f_e for every source (for example from
+ * hrir_resonance_per_source, which the paper's remark on precomputing y * f for sources
+ * known in advance motivates), each view v mixes the sources at its own directions with the
+ * reflection taps alone (no resonance is applied here):
+ *     out_v,e[n] = sum_s (u_{s,e} * g_{dir[v][s], e})[n].
+ *   u        device float [n_src][2][u_ld] (source s, ear e at u + (2 s + e) u_ld), 16-byte
+ *            aligned, u_ld % 4 == 0; u_{s,e}[0 .. len) is read.
+ *   dir      device int32 [n_views][n_src]: the direction of each source in each view (an id
+ *            out of range renders that source as silence and flags HRIR_EINVAL for hrir_sync).
+ *   full     1: out_len = len + Lg - 1, 0: out_len = len.
+ *   out      device float, view v at out + v view_ld: [2][out_ld] (row 0 left, row 1 right),
+ *            out_ld >= out_len, view_ld >= 2 out_ld; columns [0, out_len) overwritten.
+ * Each view reads u once (2 rows per source, one per ear) and applies each source's taps of
+ * one ear to each row; the partition, run lengths and fixed summation order are those of
+ * hrir_render_batch (deterministic).  Uses the filters of hrir_load_filters.
+ * ------------------------------------------------------------------------------------- */
+int hrir_render_precomputed(hrir_ctx *ctx, int n_src, int64_t len, int64_t u_ld, const float *u,
+                            int n_views, const int32_t *dir, int full, float *out, int64_t out_ld,
+                            int64_t view_ld, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * Optional kernel timing, for benchmarks.  While enabled, the library brackets each of its
  * kernel launches with CUDA events recorded on the launching stream.  hrir_kernel_times
  * waits for those events and writes, per kernel family (hrir_kernel), the accumulated

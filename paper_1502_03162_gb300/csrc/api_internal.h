@@ -22,6 +22,7 @@ struct hrir_ctx {
     bool loaded = false;
     int n_dirs = 0, refl_len = 0, k_max = 0, res_len = 0, hrir_len = 0, fft_size = 0;
     unsigned char *d_sparse = nullptr;  // (n_dirs + 1) sparse tap records
+    unsigned char *d_sparse_split = nullptr;  // (2 n_dirs + 1) one-ear records (2 d + e)
     int sparse_rec_bytes = 0;
     int sparse_nchunk = 0;   // window segments of kSparseSegment filter offsets
     int sparse_nch_pad = 0;  // segment-count array length in a record (even)
@@ -45,6 +46,8 @@ struct hrir_ctx {
     size_t mlp_ws_bytes = 0;
     void *d_fact_ws = nullptr;          // filter-production workspace (L1-NNLS fine-tune)
     size_t fact_ws_bytes = 0;
+    void *d_view_ws = nullptr;          // per-view source rows of hrir_render_precomputed
+    size_t view_ws_bytes = 0;
     int *d_status = nullptr;
 
     // optional kernel timing (hrir_set_timing)
@@ -90,9 +93,9 @@ struct KernelTimer {
     int kind;
     cudaStream_t st;
     cudaEvent_t a = nullptr;
-    KernelTimer(hrir_ctx *c, int k, cudaStream_t s) : ctx(c), kind(k), st(s)
+    KernelTimer(hrir_ctx *c, int k, cudaStream_t s, bool enabled = true) : ctx(c), kind(k), st(s)
     {
-        if (ctx->timing) {
+        if (enabled && ctx->timing) {
             a = take_event(ctx);
             cudaEventRecord(a, st);
         }
@@ -106,6 +109,26 @@ struct KernelTimer {
         a = nullptr;
     }
 };
+
+// One direct-convolution render (see mix_render in hrir_api.cu).
+struct MixJob {
+    int n_src = 0;
+    int64_t len = 0, src_ld = 0;
+    int dt = 0;
+    const void *src = nullptr;          // [n_src][src_ld] of dt, device
+    const int32_t *dir = nullptr;       // [n_src] record index per source, device
+    bool sparse = true;                 // sparse tap records, else dense HRIR records
+    const unsigned char *table = nullptr;
+    int n_dirs = 0;                     // records in table (plus one silent record)
+    const float *res = nullptr;         // resonance applied after the mix, or nullptr
+    int64_t out_len = 0;
+    float *out = nullptr;               // [2][out_ld], device
+    int64_t out_ld = 0;
+    float *scratch = nullptr;           // fixed partial-sum scratch, or nullptr: the workspace
+    size_t scratch_bytes = 0;
+    bool timed = true;                  // kernels timed by hrir_set_timing
+};
+int mix_render(hrir_ctx *ctx, const MixJob &j, cudaStream_t st);
 
 }  // namespace hrir_host
 

@@ -67,6 +67,8 @@ int mix_run_sources(const hrir_ctx *ctx, bool sparse)
 void free_tables(hrir_ctx *ctx)
 {
     cudaFree(ctx->d_sparse);
+    cudaFree(ctx->d_sparse_split);
+    ctx->d_sparse_split = nullptr;
     cudaFree(ctx->d_dense);
     cudaFree(ctx->d_res);
     cudaFree(ctx->d_tw);
@@ -249,6 +251,101 @@ int render_fft(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hrir_dtype
     return HRIR_OK;
 }
 
+// The direct-convolution render (sparse taps or dense HRIRs): the mixing kernel over
+// (tile, source) units writing partial sums, then the fixed-order reduction with the
+// resonance FIR.  Shared by hrir_render_batch, hrir_render_batch_noalloc and
+// hrir_render_precomputed, so that the three use the same partition, run lengths and
+// summation order.
+int mix_render(hrir_ctx *ctx, const MixJob &j, cudaStream_t st)
+{
+    const bool sparse = j.sparse;
+    const size_t es = dtype_size(j.dt);
+    const int nchunk = sparse ? ctx->sparse_nchunk : ctx->dense_nchunk;
+    const MixShape shape = mix_shape(sparse ? MIX_SPARSE : MIX_DENSE);
+    const int tile = shape.tile;
+    // history before each tile, a multiple of kMixBox so that tiles start on a source row
+    const int halo = (int)round_up((int64_t)nchunk * (sparse ? kSparseSegment : shape.r), kMixBox);
+    const int buf_elems = (int)round_up(halo + tile, kMixBox);
+    const int rec_bytes = sparse ? ctx->sparse_rec_bytes : 2 * ctx->dense_padded * 4;
+    const int64_t mix_len = sparse ? std::min<int64_t>(j.out_len, j.len + ctx->refl_len - 1) : j.out_len;
+    const int n_tiles = (int)((mix_len + tile - 1) / tile);
+
+    Partition part;
+    part.U = (int64_t)n_tiles * j.n_src;
+    part.P = std::min<int64_t>(ctx->num_sms, part.U);
+    part.n_src = j.n_src;
+    part.gs = mix_run_sources(ctx, sparse);
+    int slots = 0;
+    for (int t = 0; t < n_tiles; ++t) slots = std::max(slots, part.slots(t));
+    const size_t pbytes = (size_t)n_tiles * slots * 2 * tile * sizeof(float);
+    float *partial = j.scratch;
+    if (partial) {
+        if (pbytes > j.scratch_bytes)
+            return fail(ctx, HRIR_EINVAL,
+                        "this render needs %zu bytes of partial-sum scratch; the fixed array holds %zu "
+                        "(use hrir_render_batch, or fewer sources or samples per call)",
+                        pbytes, j.scratch_bytes);
+    } else {
+        int rc = grow(ctx, (void **)&ctx->d_partial, &ctx->partial_bytes, pbytes);
+        if (rc) return rc;
+        partial = ctx->d_partial;
+    }
+    size_t smem = 0;
+    const size_t extra = sparse ? (size_t)kSparseRunAccBytes : 0;
+    const int stages = pick_stages(buf_elems, (int)es, rec_bytes, extra, &smem);
+    if (stages == 0) return fail(ctx, HRIR_EINVAL, "filters too long for the shared-memory pipeline");
+    CUtensorMap tmap, tmap3;
+    int rc = make_source_map(ctx, &tmap, j.src, j.dt, j.len, j.src_ld, j.n_src);
+    if (rc) return rc;
+    rc = make_source_map3(ctx, &tmap3, tmap, j.src, j.dt, j.len, j.src_ld, j.n_src, buf_elems / kMixBox);
+    if (rc) return rc;
+
+    MixArgs a;
+    a.src = j.src;
+    a.ld = j.src_ld;
+    a.len = j.len;
+    a.n_src = j.n_src;
+    a.dir = j.dir;
+    a.n_dirs = j.n_dirs;
+    a.table = j.table;
+    a.rec_bytes = rec_bytes;
+    a.nchunk = sparse ? ctx->sparse_nch_pad : nchunk;
+    a.nseg = sparse ? ctx->sparse_nchunk : 0;
+    a.halo = halo;
+    a.buf_elems = buf_elems;
+    a.full_rows = (int)(j.len / kMixBox);
+    a.n_tiles = n_tiles;
+    a.stages = stages;
+    a.runacc_off = (int)(smem - extra);
+    a.fold = mix_fold_sources(ctx);
+    a.part = part;
+    a.partial = partial;
+    a.slots = slots;
+    a.status = ctx->d_status;
+    {
+        KernelTimer kt(ctx, sparse ? HRIR_K_MIX_SPARSE : HRIR_K_MIX_DENSE, st, j.timed);
+        CUDA_TRY(ctx, launch_mix(sparse ? MIX_SPARSE : MIX_DENSE, j.dt, tmap, tmap3, a, (int)part.P, smem, st));
+        kt.done();
+    }
+    ReduceArgs r;
+    r.partial = partial;
+    r.slots = slots;
+    r.n_tiles = n_tiles;
+    r.tile = tile;
+    r.part = part;
+    r.res = j.res;
+    r.res_len = ctx->res_len;
+    r.out_len = j.out_len;
+    r.out = j.out;
+    r.out_ld = j.out_ld;
+    {
+        KernelTimer kt(ctx, HRIR_K_REDUCE, st, j.timed);
+        CUDA_TRY(ctx, launch_reduce(r, st));
+        kt.done();
+    }
+    return HRIR_OK;
+}
+
 }  // namespace hrir_host
 
 using namespace hrir_host;
@@ -296,6 +393,7 @@ void hrir_destroy(hrir_ctx *ctx)
     cudaFree(ctx->d_stage);
     cudaFree(ctx->d_mlp_ws);
     cudaFree(ctx->d_fact_ws);
+    cudaFree(ctx->d_view_ws);
     cudaFree(ctx->d_status);
     delete ctx;
 }
@@ -455,6 +553,40 @@ int hrir_load_filters(hrir_ctx *ctx, int n_dirs, int n_ears, int refl_len, int k
                                             hrir_len, dense_padded, ctx->d_dense, 0)) != cudaSuccess)
             break;
         {
+            // one-ear records for hrir_render_precomputed: record 2d + e holds ear e's taps of
+            // direction d and no taps for the other ear
+            const size_t rows2 = 2 * rows;
+            std::vector<uint16_t> idx2(rows2 * kk, 0);
+            std::vector<float> w2(rows2 * kk, 0.f);
+            std::vector<uint8_t> nnz2(rows2, 0);
+            for (size_t r = 0; r < rows; ++r) {          // r = 2 d + e of the input tables
+                const size_t d = r / 2, ear = r % 2, dst = (2 * d + ear) * 2 + ear;
+                nnz2[dst] = tap_nnz[r];
+                for (int t = 0; t < k_max; ++t) {
+                    idx2[dst * kk + t] = tap_idx[r * k_max + t];
+                    w2[dst * kk + t] = tap_w[r * k_max + t];
+                }
+            }
+            uint16_t *d_idx2 = nullptr;
+            float *d_w2 = nullptr;
+            uint8_t *d_nnz2 = nullptr;
+            if ((e = cudaMalloc(&ctx->d_sparse_split, (size_t)(2 * n_dirs + 1) * sparse_rec)) == cudaSuccess &&
+                (e = cudaMalloc(&d_idx2, rows2 * kk * 2)) == cudaSuccess &&
+                (e = cudaMalloc(&d_w2, rows2 * kk * 4)) == cudaSuccess &&
+                (e = cudaMalloc(&d_nnz2, rows2)) == cudaSuccess &&
+                (e = cudaMemcpy(d_idx2, idx2.data(), rows2 * kk * 2, cudaMemcpyHostToDevice)) == cudaSuccess &&
+                (e = cudaMemcpy(d_w2, w2.data(), rows2 * kk * 4, cudaMemcpyHostToDevice)) == cudaSuccess &&
+                (e = cudaMemcpy(d_nnz2, nnz2.data(), rows2, cudaMemcpyHostToDevice)) == cudaSuccess &&
+                (e = launch_build_sparse_records(d_idx2, d_w2, d_nnz2, 2 * n_dirs, (int)kk, kSparseSegment,
+                                                 sparse_nseg, sparse_nseg_pad, ctx->d_sparse_split,
+                                                 sparse_rec, 0)) == cudaSuccess)
+                e = cudaDeviceSynchronize();
+            cudaFree(d_idx2);
+            cudaFree(d_w2);
+            cudaFree(d_nnz2);
+            if (e != cudaSuccess) break;
+        }
+        {
             // FFT twiddles exp(-2 pi i k / P), computed in double on the host
             std::vector<float2> tw(kFftSize);
             for (int k = 0; k < kFftSize; ++k) {
@@ -536,83 +668,21 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
     if (len > (int64_t)1 << 31) return fail(ctx, HRIR_EINVAL, "len must be < 2^31");
     if (mode == HRIR_FFT) return render_fft(ctx, n_src, len, src_ld, dt, src, dir, out_len, out, out_ld, st);
 
-    const bool sparse = mode == HRIR_SPARSE;
-    const int nchunk = sparse ? ctx->sparse_nchunk : ctx->dense_nchunk;
-    const MixShape shape = mix_shape(sparse ? MIX_SPARSE : MIX_DENSE);
-    const int tile = shape.tile;
-    // history before each tile, a multiple of kMixBox so that tiles start on a source row
-    const int halo = (int)round_up((int64_t)nchunk * (sparse ? kSparseSegment : shape.r), kMixBox);
-    const int buf_elems = (int)round_up(halo + tile, kMixBox);
-    const int rec_bytes = sparse ? ctx->sparse_rec_bytes : 2 * ctx->dense_padded * 4;
-    const int64_t mix_len = sparse ? std::min<int64_t>(out_len, len + ctx->refl_len - 1) : out_len;
-    const int n_tiles = (int)((mix_len + tile - 1) / tile);
-    size_t smem = 0;
-    const size_t extra = sparse ? (size_t)kSparseRunAccBytes : 0;
-    const int stages = pick_stages(buf_elems, (int)es, rec_bytes, extra, &smem);
-    if (stages == 0) return fail(ctx, HRIR_EINVAL, "filters too long for the shared-memory pipeline");
-    CUtensorMap tmap, tmap3;
-    int rc = make_source_map(ctx, &tmap, src, (int)dt, len, src_ld, n_src);
-    if (rc) return rc;
-    rc = make_source_map3(ctx, &tmap3, tmap, src, (int)dt, len, src_ld, n_src, buf_elems / kMixBox);
-    if (rc) return rc;
-
-    Partition part;
-    part.U = (int64_t)n_tiles * n_src;
-    part.P = std::min<int64_t>(ctx->num_sms, part.U);
-    part.n_src = n_src;
-    part.gs = mix_run_sources(ctx, sparse);
-    int slots = 0;
-    for (int t = 0; t < n_tiles; ++t) slots = std::max(slots, part.slots(t));
-    const size_t pbytes = (size_t)n_tiles * slots * 2 * tile * sizeof(float);
-    rc = grow(ctx, (void **)&ctx->d_partial, &ctx->partial_bytes, pbytes);
-    if (rc) return rc;
-
-    MixArgs a;
-    a.src = src;
-    a.ld = src_ld;
-    a.len = len;
-    a.n_src = n_src;
-    a.dir = dir;
-    a.n_dirs = ctx->n_dirs;
-    a.table = sparse ? ctx->d_sparse : reinterpret_cast<const unsigned char *>(ctx->d_dense);
-    a.rec_bytes = rec_bytes;
-    a.nchunk = sparse ? ctx->sparse_nch_pad : nchunk;
-    a.nseg = sparse ? ctx->sparse_nchunk : 0;
-    a.halo = halo;
-    a.buf_elems = buf_elems;
-    a.full_rows = (int)(len / kMixBox);
-    a.n_tiles = n_tiles;
-    a.stages = stages;
-    a.runacc_off = (int)(smem - extra);
-    a.fold = mix_fold_sources(ctx);
-    a.part = part;
-    a.partial = ctx->d_partial;
-    a.slots = slots;
-    a.status = ctx->d_status;
-    {
-        KernelTimer kt(ctx, sparse ? HRIR_K_MIX_SPARSE : HRIR_K_MIX_DENSE, st);
-        CUDA_TRY(ctx, launch_mix(sparse ? MIX_SPARSE : MIX_DENSE, (int)dt, tmap, tmap3, a, (int)part.P,
-                                 smem, st));
-        kt.done();
-    }
-
-    ReduceArgs r;
-    r.partial = ctx->d_partial;
-    r.slots = slots;
-    r.n_tiles = n_tiles;
-    r.tile = tile;
-    r.part = part;
-    r.res = sparse ? ctx->d_res : nullptr;
-    r.res_len = ctx->res_len;
-    r.out_len = out_len;
-    r.out = out;
-    r.out_ld = out_ld;
-    {
-        KernelTimer kt(ctx, HRIR_K_REDUCE, st);
-        CUDA_TRY(ctx, launch_reduce(r, st));
-        kt.done();
-    }
-    return HRIR_OK;
+    MixJob j;
+    j.n_src = n_src;
+    j.len = len;
+    j.src_ld = src_ld;
+    j.dt = (int)dt;
+    j.src = src;
+    j.dir = dir;
+    j.sparse = mode == HRIR_SPARSE;
+    j.table = j.sparse ? ctx->d_sparse : reinterpret_cast<const unsigned char *>(ctx->d_dense);
+    j.n_dirs = ctx->n_dirs;
+    j.res = j.sparse ? ctx->d_res : nullptr;
+    j.out_len = out_len;
+    j.out = out;
+    j.out_ld = out_ld;
+    return mix_render(ctx, j, st);
 }
 
 int hrir_render_batch_host(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hrir_dtype dt,

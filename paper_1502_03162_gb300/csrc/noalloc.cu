@@ -81,79 +81,25 @@ extern "C" int hrir_render_batch_noalloc(hrir_ctx *ctx, int n_src, int64_t len, 
                     "src must be 16-byte aligned with src_ld >= len and src_ld*elem_size %% 16 == 0");
     if (len > (int64_t)1 << 31) return fail(ctx, HRIR_EINVAL, "len must be < 2^31");
 
-    const bool sparse = mode == HRIR_SPARSE;
-    const MixShape shape = mix_shape(sparse ? MIX_SPARSE : MIX_DENSE);
-    const int tile = shape.tile;
-    const int nchunk = sparse ? ctx->sparse_nchunk : ctx->dense_nchunk;
-    // history before each tile, a multiple of kMixBox so that tiles start on a source row
-    const int halo = (int)round_up((int64_t)nchunk * (sparse ? kSparseSegment : shape.r), kMixBox);
-    const int buf_elems = (int)round_up(halo + tile, kMixBox);
-    const int rec_bytes = sparse ? ctx->sparse_rec_bytes : 2 * ctx->dense_padded * 4;
-    const int64_t mix_len = sparse ? std::min<int64_t>(out_len, len + ctx->refl_len - 1) : out_len;
-    const int n_tiles = (int)((mix_len + tile - 1) / tile);
-
-    Partition part;
-    part.U = (int64_t)n_tiles * n_src;
-    part.P = std::min<int64_t>(ctx->num_sms, part.U);
-    part.n_src = n_src;
-    part.gs = mix_run_sources(ctx, sparse);
-    int slots = 0;
-    for (int t = 0; t < n_tiles; ++t) slots = std::max(slots, part.slots(t));
-    const size_t need = (size_t)n_tiles * slots * 2 * tile * sizeof(float);
-    if (need > kNoAllocScratchBytes)
-        return fail(ctx, HRIR_EINVAL,
-                    "this render needs %zu bytes of partial-sum scratch; the fixed array of "
-                    "hrir_render_batch_noalloc holds %zu (use hrir_render_batch, or fewer sources "
-                    "or samples per call)",
-                    need, kNoAllocScratchBytes);
-
-    size_t smem = 0;
-    const size_t extra = sparse ? (size_t)kSparseRunAccBytes : 0;
-    const int stages = pick_stages(buf_elems, (int)es, rec_bytes, extra, &smem);
-    if (stages == 0) return fail(ctx, HRIR_EINVAL, "filters too long for the shared-memory pipeline");
-    CUtensorMap tmap, tmap3;
-    rc = make_source_map(ctx, &tmap, src, (int)dt, len, src_ld, n_src);
-    if (rc) return rc;
-    rc = make_source_map3(ctx, &tmap3, tmap, src, (int)dt, len, src_ld, n_src, buf_elems / kMixBox);
-    if (rc) return rc;
-
     // Every partial slot the reduction reads is written by the mixing kernel of this same
-    // call, so nothing in the shared scratch has to be cleared first.
-    MixArgs a;
-    a.src = src;
-    a.ld = src_ld;
-    a.len = len;
-    a.n_src = n_src;
-    a.dir = dir;
-    a.n_dirs = ctx->n_dirs;
-    a.table = sparse ? ctx->d_sparse : reinterpret_cast<const unsigned char *>(ctx->d_dense);
-    a.rec_bytes = rec_bytes;
-    a.nchunk = sparse ? ctx->sparse_nch_pad : nchunk;
-    a.nseg = sparse ? ctx->sparse_nchunk : 0;
-    a.halo = halo;
-    a.buf_elems = buf_elems;
-    a.full_rows = (int)(len / kMixBox);
-    a.n_tiles = n_tiles;
-    a.stages = stages;
-    a.runacc_off = (int)(smem - extra);
-    a.fold = mix_fold_sources(ctx);
-    a.part = part;
-    a.partial = scratch;
-    a.slots = slots;
-    a.status = ctx->d_status;
-    HRIR_CUDA_TRY(ctx, launch_mix(sparse ? MIX_SPARSE : MIX_DENSE, (int)dt, tmap, tmap3, a,
-                                  (int)part.P, smem, st));
-    ReduceArgs r;
-    r.partial = scratch;
-    r.slots = slots;
-    r.n_tiles = n_tiles;
-    r.tile = tile;
-    r.part = part;
-    r.res = sparse ? ctx->d_res : nullptr;
-    r.res_len = ctx->res_len;
-    r.out_len = out_len;
-    r.out = out;
-    r.out_ld = out_ld;
-    HRIR_CUDA_TRY(ctx, launch_reduce(r, st));
-    return HRIR_OK;
+    // call, so nothing in the shared scratch has to be cleared first.  The kernels are not
+    // timed (timing would create CUDA events).
+    MixJob j;
+    j.n_src = n_src;
+    j.len = len;
+    j.src_ld = src_ld;
+    j.dt = (int)dt;
+    j.src = src;
+    j.dir = dir;
+    j.sparse = mode == HRIR_SPARSE;
+    j.table = j.sparse ? ctx->d_sparse : reinterpret_cast<const unsigned char *>(ctx->d_dense);
+    j.n_dirs = ctx->n_dirs;
+    j.res = j.sparse ? ctx->d_res : nullptr;
+    j.out_len = out_len;
+    j.out = out;
+    j.out_ld = out_ld;
+    j.scratch = scratch;
+    j.scratch_bytes = kNoAllocScratchBytes;
+    j.timed = false;
+    return mix_render(ctx, j, st);
 }

@@ -62,6 +62,7 @@ SIGNATURES = {
     "hrir_resonance_per_source": ([_vp, _i, _i64, _i64, _i, _vp, _i, _vp, _i64, _vp], _i),
     "hrir_sparsify": ([_vp, _i, _i, _i, _i, _vp, _vp, ctypes.c_float, ctypes.c_float,
                        ctypes.c_float, _vp, _vp, _vp], _i),
+    "hrir_render_precomputed": ([_vp, _i, _i64, _i64, _vp, _i, _vp, _i, _vp, _i64, _i64, _vp], _i),
     "hrir_set_timing": ([_vp, _i], _i),
     "hrir_kernel_times": ([_vp, _vp, _vp, _i], _i),
 }
@@ -250,6 +251,7 @@ def hrir_load_filters(ctx, tap_idx, tap_w, tap_nnz, refl_len: int, res, fft_size
         tap_nnz.ctypes.data, res.shape[1], res.ctypes.data, fft_size)
     _check(ctx, rc)
     _RES_LEN[ctx] = res.shape[1]
+    _REFL_LEN[ctx] = int(refl_len)
 
 
 def hrir_out_len(ctx, length: int, full: bool = True) -> int:
@@ -564,7 +566,42 @@ def hrir_sparsify(ctx, X, f, refl_len: int, lam: float, sigma: float = 0.0, thre
     return G, nnz
 
 
+def hrir_render_precomputed(ctx, u, dirs, full=True, length=None, out=None, stream=None):
+    """u: CUDA float32 [S][2][u_ld] (u[s, e] = y_s * f_e, e.g. from hrir_resonance_per_source);
+    dirs: CUDA int32 [n_views][S].  Returns out CUDA float32 [n_views][2][out_len]: each view
+    mixes u through its directions' reflection taps (no resonance added)."""
+    import torch
+    _check_tensor(u, "u", cuda=True, dtypes=(torch.float32,), dim=3, unit_stride=True)
+    S = u.shape[0]
+    _require(u.shape[1] == 2, f"u: {u.shape[1]} ears, expected 2")
+    _require(S == 0 or u.stride(0) == 2 * u.stride(1),
+             "u: the two ears of a source must be adjacent rows ([S][2][len] layout)")
+    u_ld = u.stride(1) if S else u.shape[2]
+    L = u.shape[2] if length is None else int(length)
+    _require(0 <= L <= u.shape[2], f"length {L} outside u's {u.shape[2]} samples")
+    _check_tensor(dirs, "dirs", cuda=True, dtypes=(torch.int32,), dim=2, contiguous=True)
+    _require(dirs.shape[1] == S, f"dirs: {dirs.shape[1]} sources per view, expected {S}")
+    V = dirs.shape[0]
+    out_len = (L + _refl_len(ctx) - 1 if L > 0 else 0) if full else L
+    if out is None:
+        out = torch.empty((V, 2, max(out_len, 1)), dtype=torch.float32, device=u.device)
+    _check_tensor(out, "out", cuda=True, dtypes=(torch.float32,), min_shape=(V, 2, out_len),
+                  unit_stride=True)
+    _require(V == 0 or out.stride(0) >= 2 * out.stride(1), "out: views overlap")
+    rc = load_library().hrir_render_precomputed(
+        ctx, S, L, u_ld, u.data_ptr(), V, dirs.data_ptr(), int(full), out.data_ptr(),
+        out.stride(1) if V else max(out_len, 1), out.stride(0) if V else 2 * max(out_len, 1),
+        _stream_handle(stream))
+    _check(ctx, rc)
+    return out[:, :, :out_len]
+
+
 _RES_LEN = {}
+_REFL_LEN = {}
+
+
+def _refl_len(ctx) -> int:
+    return _REFL_LEN[ctx]
 
 
 def _res_len(ctx) -> int:

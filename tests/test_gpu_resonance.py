@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_1502_03162_gb300 import synth
-from tests.gpu_util import TOL, tables
+from tests.gpu_util import TOL, assert_close, tables
 
 pytestmark = pytest.mark.gpu
 
@@ -57,3 +57,40 @@ def test_resonance_gemm_rejects_fp32_sources(rend):
     y = torch.zeros((2, 64), device="cuda")
     with pytest.raises(ValueError):
         hrir.hrir_resonance_per_source(rend.ctx, y)
+
+
+@pytest.mark.parametrize("dt,S,L,n_views", [("bfloat16", 37, 20011, 3), ("float16", 130, 4099, 2),
+                                            ("bfloat16", 3, 200, 1)])
+def test_precomputed_resonance_rendered_to_several_views(rend, dt, S, L, n_views):
+    """The order (y * f) * g of Eq. 2: u = y * f once per source on the tensor cores, then each
+    view mixes u through its own directions' reflection taps alone.  Every view equals the
+    oracle's mix in that order (and so the direct render of the same sources, Eq. 2)."""
+    from paper_1502_03162_gb300 import hrir
+    rng = np.random.default_rng(S + L + n_views)
+    n_dirs = 50
+    _, idx, w, nnz, res = tables(rng, n_dirs, 16)
+    rend.load_filters(idx, w, nnz, 200, res)
+    ld = (L + 7) // 8 * 8
+    y = np.zeros((S, ld), np.float32)
+    y[:, :L] = synth.sources_ar1(rng, S, L)
+    yq = torch.from_numpy(y).to(getattr(torch, dt))
+    ydq = yq.float().numpy()
+    u = hrir.hrir_resonance_per_source(rend.ctx, yq.cuda(), full=True, length=L)
+    dirs = np.stack([synth.directions(rng, S, n_dirs) for _ in range(n_views)])
+    dirs[0, 0] = n_dirs + 5                          # an id out of range: that source is silent
+    out = hrir.hrir_render_precomputed(rend.ctx, u, torch.from_numpy(dirs).cuda())
+    assert rend.sync() == hrir.HRIR_EINVAL            # the bad id is flagged ...
+    assert rend.sync() == 0
+    out = out.cpu().numpy()
+    assert out.shape == (n_views, 2, L + 230)
+    for v in range(n_views):
+        keep = np.ones(S, bool)
+        if v == 0:
+            keep[0] = False                          # ... and rendered as silence
+        ref = oracle.render_sparse(ydq[keep], dirs[v][keep], idx, w, nnz, 200, res, length=L, order=1)
+        assert_close(out[v], ref, what=f"{dt} view {v}")
+    same = hrir.hrir_render_precomputed(rend.ctx, u, torch.from_numpy(dirs[1:]).cuda(), full=False)
+    assert rend.sync() == 0
+    Lu = u.shape[2]                                  # u holds the full y * f: L + Lf - 1 samples
+    assert same.shape == (n_views - 1, 2, Lu)
+    assert_close(same.cpu().numpy()[0], out[1, :, :Lu], what="first len(u) samples")
