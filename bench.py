@@ -698,10 +698,15 @@ def main():
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     e2e_ms = max_over_ranks(e2e_ms)
     h2d = int(S * host.shape[1] * 4 + S * 4)
+    # the host link's own rate: one plain copy of the same pinned batch, CUDA events
+    copy_ms = time_steps(lambda: src.copy_(host, non_blocking=True), 3, 1, torch, barrier)
+    link_gbs = S * host.shape[1] * 4 / (copy_ms / 1e3) / 1e9
+    e2e_link = h2d / (e2e_ms / 1e3) / 1e9
     result["e2e"] = {"value": ranks.whole_job(units, e2e_ms), "unit": "source-ear samples/s",
                      "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d,
                      "d2h_bytes_per_step": int(2 * (L + 230) * 4),
-                     "host_link_gbs": h2d / (e2e_ms / 1e3) / 1e9}
+                     "host_link_gbs": e2e_link, "host_copy_gbs": link_gbs,
+                     "host_link_frac": e2e_link / link_gbs}
 
     if not args.no_extras:
         result["sparsified"] = bench_sparsified(rend, torch, src, dirs, L, max(3, args.steps // 5),

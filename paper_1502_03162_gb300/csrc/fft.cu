@@ -13,8 +13,10 @@
 //    flushed to partial spectra, like the direct kernels.
 //  * fft_out_kernel: per frame, fixed-order compensated sum of the partial spectra, one
 //    complex inverse FFT carrying both ears (z = X_L + i X_R), output positions G .. P-1.
-// The FFT is a radix-8 Stockham (autosort) transform of P = 4096 points by 512 threads,
-// four passes through a padded shared-memory buffer, twiddles from a table.
+// fft_mix_kernel's FFT is a radix-16 Stockham (autosort) transform of P = 4096 points by 256
+// threads in three passes (two exchanges through padded shared-memory buffers, ping-pong);
+// the spectra builder and the inverse transform use a radix-8 Stockham transform by 512
+// threads in four passes.  Twiddles come from a table computed in double on the host.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -137,47 +139,104 @@ template <>
 __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
 
 // ---- forward FFT + frequency-domain mix ------------------------------------------------------
-// Shared memory: two TMA stages of [kN/256 boxes][2 rows][256] source samples, the padded
-// FFT buffer, two mbarriers.
+// One (frame, source pair) unit per step of a persistent CTA of 256 threads: the 4096-point
+// complex FFT of z = y_a + i y_b as a radix-16 Stockham transform (three passes; thread t holds
+// 16 points per pass), the split into the two real spectra, and the multiply-accumulate with
+// each source's HRIR spectra per ear (the mix happens in the frequency domain).
+constexpr int kT16 = kN / 16;        // 256 threads
+
+// forward 4-point DFT (exp(-2 pi i nk / 4)) in place
+__device__ __forceinline__ void dft4(float2 &a, float2 &b, float2 &c, float2 &d)
+{
+    const float2 t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = mul_mi(csub(b, d));
+    a = cadd(t0, t2);
+    c = csub(t0, t2);
+    b = cadd(t1, t3);
+    d = csub(t1, t3);
+}
+
+// forward 16-point DFT in registers, natural order in and out: four DFT4s over (n, n+4, n+8,
+// n+12), twiddles exp(-2 pi i n m / 16), four DFT4s over n; output index m + 4 k
+__device__ __forceinline__ void dft16(float2 (&u)[16])
+{
+    dft4(u[0], u[4], u[8], u[12]);
+    dft4(u[1], u[5], u[9], u[13]);
+    dft4(u[2], u[6], u[10], u[14]);
+    dft4(u[3], u[7], u[11], u[15]);
+    // u[n + 4 m] *= w16^(n m), w16^j = (cos(2 pi j / 16), -sin(2 pi j / 16))
+    const float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+    u[5] = cmul(u[5], make_float2(c1, -s1));        // n 1, m 1
+    u[9] = cmul(u[9], make_float2(h, -h));          // n 1, m 2
+    u[13] = cmul(u[13], make_float2(s1, -c1));      // n 1, m 3
+    u[6] = cmul(u[6], make_float2(h, -h));          // n 2, m 1
+    u[10] = mul_mi(u[10]);                          // n 2, m 2: w16^4 = -i
+    u[14] = cmul(u[14], make_float2(-h, -h));       // n 2, m 3: w16^6
+    u[7] = cmul(u[7], make_float2(s1, -c1));        // n 3, m 1: w16^3
+    u[11] = cmul(u[11], make_float2(-h, -h));       // n 3, m 2: w16^6
+    u[15] = cmul(u[15], make_float2(-c1, s1));      // n 3, m 3: w16^9
+    dft4(u[0], u[1], u[2], u[3]);
+    dft4(u[4], u[5], u[6], u[7]);
+    dft4(u[8], u[9], u[10], u[11]);
+    dft4(u[12], u[13], u[14], u[15]);
+    // now u[m 4 + k] holds X[m + 4 k]: transpose the 4 x 4 index
+    float2 t;
+    t = u[1]; u[1] = u[4]; u[4] = t;
+    t = u[2]; u[2] = u[8]; u[8] = t;
+    t = u[3]; u[3] = u[12]; u[12] = t;
+    t = u[6]; u[6] = u[9]; u[9] = t;
+    t = u[7]; u[7] = u[13]; u[13] = t;
+    t = u[11]; u[11] = u[14]; u[14] = t;
+}
+
+// Shared memory: one TMA stage [kN/256 boxes][2 rows][256] of source samples, two padded FFT
+// buffers (ping-pong), the twiddle tables, an mbarrier.
 template <typename T>
-__global__ void __launch_bounds__(kT, kFftCtasPerSm)
+__global__ void __launch_bounds__(kT16, kFftCtasPerSm)
     fft_mix_kernel(const __grid_constant__ CUtensorMap tmap, const FftArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    T *stage = reinterpret_cast<T *>(smem);                                  // [2][2*kN]
-    float2 *buf = reinterpret_cast<float2 *>(smem + 2 * 2 * kN * sizeof(T));  // [kPadded]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(buf + kPadded);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2);
+    T *stage = reinterpret_cast<T *>(smem);                                  // [2 * kN]
+    float2 *bufA = reinterpret_cast<float2 *>(smem + 2 * kN * sizeof(T));     // [kPadded]
+    float2 *bufB = bufA + kPadded;                                            // [kPadded]
+    // twiddles w = exp(-2 pi i / kN): tw16[r][a] = w^(16 a r), tw1[r][b] = w^(b r), so that
+    // pass 2 reads w^(16 (t % 16) r) = tw16[r][t % 16] and pass 3 forms w^(t r) =
+    // tw16[r][t / 16] tw1[r][t % 16] (two roundings), both conflict-free or broadcast
+    float2 *tw16 = bufB + kPadded;                                            // [16][16]
+    float2 *tw1 = tw16 + 256;                                                 // [16][16]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tw1 + 256);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bar + 1);
     const int tid = threadIdx.x;
     if (tid == 0) {
         prefetch_tensormap(&tmap);
-        mbar_init(smem_addr(&bars[0]), 1);
-        mbar_init(smem_addr(&bars[1]), 1);
+        mbar_init(smem_addr(bar), 1);
         *abort_flag = 0;
         mbar_fence_init();
+    }
+    {
+        const int r = tid >> 4, c = tid & 15;
+        tw16[tid] = __ldg(a.tw + ((16 * c * r) & (kN - 1)));
+        tw1[tid] = __ldg(a.tw + c * r);
     }
     __syncthreads();
     const int64_t u_begin = a.part.first(blockIdx.x), u_end = a.part.first(blockIdx.x + 1);
     const int n_pairs = a.part.n_src;
 
-    auto issue = [&](int64_t u, int st) {
+    auto issue = [&](int64_t u) {
         const int j = (int)(u / n_pairs);
         const int p = (int)(u - (int64_t)j * n_pairs);
         const int x0 = j * a.hop - a.guard;
-        const uint32_t bar = smem_addr(&bars[st]);
-        mbar_arrive_expect_tx(bar, (uint32_t)(2 * kN * sizeof(T)));
+        mbar_arrive_expect_tx(smem_addr(bar), (uint32_t)(2 * kN * sizeof(T)));
         for (int b = 0; b < kN / 256; ++b)
-            tma_load_2d(smem_addr(stage + (size_t)st * 2 * kN + b * 512), &tmap, x0 + b * 256, 2 * p, bar);
+            tma_load_2d(smem_addr(stage + b * 512), &tmap, x0 + b * 256, 2 * p, smem_addr(bar));
     };
-    if (tid == 0 && u_begin < u_end) issue(u_begin, 0);
+    if (tid == 0 && u_begin < u_end) issue(u_begin);
 
-    float2 accL[4], accR[4], accL5 = make_float2(0.f, 0.f), accR5 = make_float2(0.f, 0.f);
+    float2 accL[8], accR[8], accL8 = make_float2(0.f, 0.f), accR8 = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) accL[q] = accR[q] = make_float2(0.f, 0.f);
+    for (int q = 0; q < 8; ++q) accL[q] = accR[q] = make_float2(0.f, 0.f);
     int cur_f = -1, slot = 0, run_n = 0;
+    int64_t issued_to = u_begin + 1;     // units whose loads have been issued: [u_begin, issued_to)
     for (int64_t u = u_begin, k = 0; u < u_end; ++u, ++k) {
-        const int st = (int)(k & 1);
-        if (tid == 0 && u + 1 < u_end) issue(u + 1, st ^ 1);
         const int f = (int)(u / n_pairs);
         const int p = (int)(u - (int64_t)f * n_pairs);
         if (f != cur_f) {
@@ -185,30 +244,58 @@ __global__ void __launch_bounds__(kT, kFftCtasPerSm)
             slot = a.part.slot_base(blockIdx.x, f);
             run_n = 0;
         }
-        const bool ok =
-            mbar_wait_bounded(smem_addr(&bars[st]), (uint32_t)((k >> 1) & 1), abort_flag, a.status);
+        const bool ok = mbar_wait_bounded(smem_addr(bar), (uint32_t)(k & 1), abort_flag, a.status);
         if (__syncthreads_or(!ok)) {  // every thread leaves together: no one is left at a barrier
-            if (tid == 0) {
-                // let the copies still in flight (this unit's and the prefetched one) land
-                for (int64_t kk = k; kk <= k + 1 && u_begin + kk < u_end; ++kk) {
-                    const uint32_t fb = smem_addr(&bars[kk & 1]);
-                    const uint64_t t0 = global_timer_ns();
-                    while (!mbar_try_wait(fb, (uint32_t)((kk >> 1) & 1)) &&
-                           global_timer_ns() - t0 < kWaitLimitNs) {
-                    }
+            if (tid == 0 && issued_to > u) {
+                // let the copy in flight land (bounded)
+                const uint64_t t0 = global_timer_ns();
+                while (!mbar_try_wait(smem_addr(bar), (uint32_t)(k & 1)) && global_timer_ns() - t0 < kWaitLimitNs) {
                 }
             }
             break;
         }
-        const T *sa = stage + (size_t)st * 2 * kN;
-        float2 v[8];
+        // The two FFT buffers change roles from unit to unit (X for the first pass's output and
+        // the mirror bins, Y for the second pass's output), so that a unit's first stores never
+        // touch the buffer the previous unit's multiply-accumulate still reads: three CTA
+        // barriers per unit.
+        float2 *X = (k & 1) ? bufB : bufA;
+        float2 *Y = (k & 1) ? bufA : bufB;
+        // pass 1 (p = 1): z[t + 256 r] from the stage, DFT16, to X at 16 t + r
+        float2 v[16];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int n = tid + r * kT;
-            const int base = (n >> 8) * 512 + (n & 255);
-            v[r] = make_float2(to_f<T>(sa[base]), to_f<T>(sa[base + 256]));
+        for (int r = 0; r < 16; ++r)
+            v[r] = make_float2(to_f<T>(stage[r * 512 + tid]), to_f<T>(stage[r * 512 + 256 + tid]));
+        dft16(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) X[pad(16 * tid + r)] = v[r];
+        __syncthreads();                                     // stage consumed, X written
+        if (tid == 0 && u + 1 < u_end) {
+            issue(u + 1);                                    // the next unit's source, now
+            issued_to = u + 2;
         }
-        fft_forward(v, buf, a.tw);
+        // pass 2 (p = 16): X -> Y
+        {
+            const int kk = tid & 15;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = X[pad(tid + 256 * r)];
+#pragma unroll
+            for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw16[16 * r + kk]);
+            dft16(v);
+            const int j = (tid - kk) * 16 + kk;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) Y[pad(j + 16 * r)] = v[r];
+        }
+        __syncthreads();                                     // Y written
+        // pass 3 (p = 256): Y -> registers: v[r] = Z[t + 256 r]
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = Y[pad(tid + 256 * r)];
+#pragma unroll
+        for (int r = 1; r < 16; ++r)
+            v[r] = cmul(v[r], cmul(tw16[16 * r + (tid >> 4)], tw1[16 * r + (tid & 15)]));
+        dft16(v);
+        // the mirror bins Z[4096 - k] of every k < 2048 lie in the upper halves (r >= 8)
+#pragma unroll
+        for (int r = 8; r < 16; ++r) X[pad(tid + 256 * r)] = v[r];
         // directions of the pair (the silent record beyond the last source or out of range)
         const int s0 = 2 * p, s1 = 2 * p + 1;
         int d0 = __ldg(a.dir + s0);
@@ -226,38 +313,61 @@ __global__ void __launch_bounds__(kT, kFftCtasPerSm)
         }
         const float2 *h0 = a.spec + (size_t)d0 * 2 * kFftBinsPadded;
         const float2 *h1 = a.spec + (size_t)d1 * 2 * kFftBinsPadded;
+        // the spectra of the first four bins are requested before the barrier (their latency
+        // overlaps it); the other four after
+        float2 hp[4][4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int kb = tid + q * kT;
-            float2 y0, y1;
-            split_real_pair(buf[pad(kb)], buf[pad((kN - kb) & (kN - 1))], y0, y1);
-            accL[q] = cadd(accL[q], cadd(cmul(y0, __ldg(h0 + kb)), cmul(y1, __ldg(h1 + kb))));
-            accR[q] = cadd(accR[q], cadd(cmul(y0, __ldg(h0 + kFftBinsPadded + kb)),
-                                         cmul(y1, __ldg(h1 + kFftBinsPadded + kb))));
+            const int kb = tid + 256 * q;
+            hp[q][0] = __ldg(h0 + kb);
+            hp[q][1] = __ldg(h1 + kb);
+            hp[q][2] = __ldg(h0 + kFftBinsPadded + kb);
+            hp[q][3] = __ldg(h1 + kFftBinsPadded + kb);
         }
-        if (tid == 0) {
+        __syncthreads();                                     // mirrors written
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int kb = tid + 256 * q;
+            const float2 zm = (tid == 0) ? (q == 0 ? v[0] : X[pad(kN - 256 * q)]) : X[pad(kN - kb)];
+            float2 y0, y1;
+            split_real_pair(v[q], zm, y0, y1);
+            float2 g0, g1, g2, g3;
+            if (q < 4) {
+                g0 = hp[q & 3][0];
+                g1 = hp[q & 3][1];
+                g2 = hp[q & 3][2];
+                g3 = hp[q & 3][3];
+            } else {
+                g0 = __ldg(h0 + kb);
+                g1 = __ldg(h1 + kb);
+                g2 = __ldg(h0 + kFftBinsPadded + kb);
+                g3 = __ldg(h1 + kFftBinsPadded + kb);
+            }
+            accL[q] = cadd(accL[q], cadd(cmul(y0, g0), cmul(y1, g1)));
+            accR[q] = cadd(accR[q], cadd(cmul(y0, g2), cmul(y1, g3)));
+        }
+        if (tid == 0) {                                      // the Nyquist bin, its own mirror
             const int kb = kN / 2;
             float2 y0, y1;
-            split_real_pair(buf[pad(kb)], buf[pad(kb)], y0, y1);
-            accL5 = cadd(accL5, cadd(cmul(y0, __ldg(h0 + kb)), cmul(y1, __ldg(h1 + kb))));
-            accR5 = cadd(accR5, cadd(cmul(y0, __ldg(h0 + kFftBinsPadded + kb)),
+            split_real_pair(v[8], v[8], y0, y1);
+            accL8 = cadd(accL8, cadd(cmul(y0, __ldg(h0 + kb)), cmul(y1, __ldg(h1 + kb))));
+            accR8 = cadd(accR8, cadd(cmul(y0, __ldg(h0 + kFftBinsPadded + kb)),
                                      cmul(y1, __ldg(h1 + kFftBinsPadded + kb))));
         }
-        __syncthreads();  // buf is rewritten by the next unit
         ++run_n;
         const bool frame_end = (u + 1 == u_end) || ((u + 1) / n_pairs != f);
         if (run_n == a.part.gs || frame_end) {
             float2 *ps = a.partial + ((size_t)f * a.slots + slot) * 2 * kFftBinsPadded;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                ps[tid + q * kT] = accL[q];
-                ps[kFftBinsPadded + tid + q * kT] = accR[q];
+            for (int q = 0; q < 8; ++q) {
+                ps[tid + 256 * q] = accL[q];
+                ps[kFftBinsPadded + tid + 256 * q] = accR[q];
                 accL[q] = accR[q] = make_float2(0.f, 0.f);
             }
             if (tid == 0) {
-                ps[kN / 2] = accL5;
-                ps[kFftBinsPadded + kN / 2] = accR5;
-                accL5 = accR5 = make_float2(0.f, 0.f);
+                ps[kN / 2] = accL8;
+                ps[kFftBinsPadded + kN / 2] = accR8;
+                accL8 = accR8 = make_float2(0.f, 0.f);
             }
             ++slot;
             run_n = 0;
@@ -310,7 +420,7 @@ __global__ void __launch_bounds__(kT) fft_out_kernel(const FftOutArgs a)
 
 size_t fft_mix_smem_bytes(int elem_bytes)
 {
-    return (size_t)2 * 2 * kN * elem_bytes + (size_t)kPadded * sizeof(float2) + 2 * 8 + 16;
+    return (size_t)2 * kN * elem_bytes + (2 * (size_t)kPadded + 512) * sizeof(float2) + 8 + 16;
 }
 
 cudaError_t launch_build_spectra(const float *dense, int padded_len, int hrir_len, int n_records,
@@ -327,7 +437,7 @@ static cudaError_t launch_fft_mix_t(const CUtensorMap &tmap, const FftArgs &a, i
     auto k = fft_mix_kernel<T>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, kT, smem, st>>>(tmap, a);
+    k<<<grid, kT16, smem, st>>>(tmap, a);
     return cudaGetLastError();
 }
 
