@@ -145,14 +145,37 @@ __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v)
 // each source's HRIR spectra per ear (the mix happens in the frequency domain).
 constexpr int kT16 = kN / 16;        // 256 threads
 
+// complex addition and subtraction as one packed FP32 instruction each (add/sub.rn.f32x2:
+// two independent round-to-nearest operations, the same results as two scalar ones)
+__device__ __forceinline__ float2 padd(float2 a, float2 b)
+{
+    uint64_t x, y, r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.x), "f"(b.y));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+    float2 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+    return o;
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b)
+{
+    uint64_t x, y, r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+    float2 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+    return o;
+}
+
 // forward 4-point DFT (exp(-2 pi i nk / 4)) in place
 __device__ __forceinline__ void dft4(float2 &a, float2 &b, float2 &c, float2 &d)
 {
-    const float2 t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = mul_mi(csub(b, d));
-    a = cadd(t0, t2);
-    c = csub(t0, t2);
-    b = cadd(t1, t3);
-    d = csub(t1, t3);
+    const float2 t0 = padd(a, c), t1 = psub(a, c), t2 = padd(b, d), t3 = mul_mi(psub(b, d));
+    a = padd(t0, t2);
+    c = psub(t0, t2);
+    b = padd(t1, t3);
+    d = psub(t1, t3);
 }
 
 // forward 16-point DFT in registers, natural order in and out: four DFT4s over (n, n+4, n+8,
@@ -343,8 +366,8 @@ __global__ void __launch_bounds__(kT16, kFftCtasPerSm)
                 g2 = __ldg(h0 + kFftBinsPadded + kb);
                 g3 = __ldg(h1 + kFftBinsPadded + kb);
             }
-            accL[q] = cadd(accL[q], cadd(cmul(y0, g0), cmul(y1, g1)));
-            accR[q] = cadd(accR[q], cadd(cmul(y0, g2), cmul(y1, g3)));
+            accL[q] = padd(accL[q], padd(cmul(y0, g0), cmul(y1, g1)));
+            accR[q] = padd(accR[q], padd(cmul(y0, g2), cmul(y1, g3)));
         }
         if (tid == 0) {                                      // the Nyquist bin, its own mirror
             const int kb = kN / 2;
