@@ -49,17 +49,10 @@ constexpr int kRunSources = 64;                   // max sources per partial slo
 //    flushed to the run's partial slot every kRunSources sources (sums of ~64 terms at
 //    either level);
 //  * dense kernel (231 products per source): runs of kDenseRunSources sources;
-//  * moving-source kernel (2K products per source): runs of run_sources(2K) sources, at most
-//    kAccumTerms products.
+//  * moving-source kernel: each source's taps are summed in fresh registers, so its runs of
+//    kRunSources sources are already sums of kRunSources terms.
 constexpr int kFoldTerms = 64;
 constexpr int kDenseRunSources = 8;
-constexpr int kAccumTerms = 512;
-// Sources per accumulation run for `terms` products per source and output.
-inline int run_sources(int terms)
-{
-    const int g = kAccumTerms / (terms > 0 ? terms : 1);
-    return g < 1 ? 1 : (g > kRunSources ? kRunSources : g);
-}
 
 enum MixMode : int { MIX_SPARSE = 0, MIX_DENSE = 1 };
 

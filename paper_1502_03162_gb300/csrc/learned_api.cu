@@ -314,7 +314,9 @@ int hrir_render_moving(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, co
     part.U = (int64_t)n_tiles * n_src;
     part.P = std::min<int64_t>((int64_t)ctx->num_sms * moving_ctas_per_sm(smem), part.U);
     part.n_src = n_src;
-    part.gs = run_sources(2 * std::max(k_max, 1));   // two filters per output (the crossfade)
+    // each source's taps are summed in fresh registers and its contribution is one term of
+    // the run's sum: runs of kRunSources sources are sums of that many terms
+    part.gs = kRunSources;
     int slots = 0;
     for (int t = 0; t < n_tiles; ++t) slots = std::max(slots, part.slots(t));
     const size_t pbytes = (size_t)n_tiles * slots * 2 * kMovTile * sizeof(float);

@@ -217,3 +217,38 @@ def test_resonance_mlp_filters_admit_reject(lib):
     _rejected(lib, hrir.hrir_stream_admit, CTX, 1, 1, np.zeros(10, np.float64), 0)
     _rejected(lib, hrir.hrir_stream_admit, CTX, 1, 1, np.zeros(20, np.float32)[::2], 0)
     _rejected(lib, hrir.hrir_stream_admit, CTX, 1, 1, fc((10,)), 0)
+
+
+# ---- filter production and the precomputed-resonance views ---------------------------------
+def test_sparsify_and_views_valid(lib, monkeypatch):
+    monkeypatch.setitem(hrir._REFL_LEN, CTX, 200)
+    X, f = fc((1250, 2, 231)), fc((2, 32))
+    G, nnz = hrir.hrir_sparsify(CTX, X, f, 200, 1e-3, 60.0, 1e-4, stream=0)
+    a = last(lib, "hrir_sparsify")
+    assert a[1:5] == (1250, 2, 231, 200) and tuple(G.shape) == (1250, 2, 200)
+    assert tuple(nnz.shape) == (1250, 2)
+    S, Lu = 37, 20042
+    u = fc((S, 2, 20044))
+    out = hrir.hrir_render_precomputed(CTX, u, fc((3, S), torch.int32), length=Lu, stream=0)
+    a = last(lib, "hrir_render_precomputed")
+    assert a[1:4] == (S, Lu, 20044) and a[5] == 3 and tuple(out.shape) == (3, 2, Lu + 199)
+    assert a[9] == out.stride(1) and a[10] == out.stride(0)
+
+
+def test_sparsify_and_views_reject(lib, monkeypatch):
+    monkeypatch.setitem(hrir._REFL_LEN, CTX, 200)
+    sp = lambda *a, **k: _rejected(lib, hrir.hrir_sparsify, CTX, *a, stream=0, **k)  # noqa: E731
+    sp(torch.zeros((10, 2, 231)), fc((2, 32)), 200, 1e-3)            # host HRIRs
+    sp(fc((10, 3, 231)), fc((3, 32)), 200, 1e-3)                     # three ears
+    sp(fc((10, 2, 231)), fc((2, 31)), 200, 1e-3)                     # resonance length
+    sp(fc((10, 2, 231)), fc((2, 32)), 240, 1e-3)                     # Lg > M
+    sp(fc((10, 2, 231)), fc((2, 32)), 200, 1e-3, G=fc((10, 2, 199)))  # output rows
+    sp(fc((10, 2, 231)), fc((2, 32)), 200, 1e-3, nnz=fc((10, 2), torch.int64))
+    S = 5
+    v = lambda *a, **k: _rejected(lib, hrir.hrir_render_precomputed, CTX, *a, stream=0, **k)  # noqa: E731
+    v(fc((S, 1, 1000)), fc((2, S), torch.int32))                     # one ear
+    v(fc((S, 2, 1000)), fc((2, S + 1), torch.int32))                 # directions per view
+    v(fc((S, 2, 1000)), fc((2, S), torch.int64))                     # direction dtype
+    v(fc((S, 2, 1000)), fc((2, S), torch.int32), length=1001)        # longer than u
+    v(fc((S, 2, 1000)), fc((2, S), torch.int32), out=fc((2, 2, 1198)))  # output too short
+    v(FakeCuda(torch.zeros((2, S, 1000)).transpose(0, 1)), fc((2, S), torch.int32))  # ears apart
