@@ -146,7 +146,7 @@ int64_t hrir_out_len(const hrir_ctx *ctx, int64_t len, int full);
  *   stream  cudaStream_t to enqueue on.
  * Every source is read once per render; the mix is deterministic (fixed summation order
  * for a given device and shape).  Accuracy: no FP32 sum in the mix runs over more than a
- * few hundred products (HRIR_SPARSE: registers folded every ~64 products into per-lane
+ * few hundred products (HRIR_SPARSE: registers folded every ~128 products into per-lane
  * accumulators, flushed every 64 sources; HRIR_DENSE: runs of 8 sources), the runs'
  * partial sums are added with compensation (Kahan) and the resonance stage is a
  * compensated dot product.  n_src == 0 writes zeros; len == 0 writes nothing.

@@ -46,12 +46,12 @@ constexpr int kRunSources = 64;                   // max sources per partial slo
 // short or split in two levels:
 //  * sparse kernel: its tap registers are folded every kFoldTerms products (fold = max(1,
 //    kFoldTerms / K) sources) into a per-lane FP32 accumulator in shared memory, which is
-//    flushed to the run's partial slot every kRunSources sources (sums of ~64 terms at
-//    either level);
+//    flushed to the run's partial slot every kRunSources sources (sums of at most ~128
+//    and 64 terms at the two levels);
 //  * dense kernel (231 products per source): runs of kDenseRunSources sources;
 //  * moving-source kernel: each source's taps are summed in fresh registers, so its runs of
 //    kRunSources sources are already sums of kRunSources terms.
-constexpr int kFoldTerms = 64;
+constexpr int kFoldTerms = 128;
 constexpr int kDenseRunSources = 8;
 
 enum MixMode : int { MIX_SPARSE = 0, MIX_DENSE = 1 };
@@ -186,7 +186,10 @@ cudaError_t launch_features_layer1(int n_rows, const float *dirs, const float *W
 cudaError_t launch_output_grad(int64_t n_rows, int refl_len, const float *g, const float *tgt,
                                const float *z4, int64_t ldz, float inv_b, float *dz, float *partial,
                                int n_partial, float *loss, cudaStream_t st);
-cudaError_t launch_colsum(int64_t rows, int N, const float *D, int64_t ldd, float *out, cudaStream_t st);
+// out[n] = sum_b D[b][n] for n < N, deterministic; P: workspace of kColsumMaxChunks * N floats
+constexpr int kColsumMaxChunks = 64;
+cudaError_t launch_colsum(int64_t rows, int N, const float *D, int64_t ldd, float *P, float *out,
+                          cudaStream_t st);
 cudaError_t launch_split_reduce(int splits, int M, int N, const float *P, float *out, cudaStream_t st);
 cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v, float lr, float b1,
                         float b2, float eps, float c1, float c2, cudaStream_t st);

@@ -202,7 +202,9 @@ int hrir_mlp_backward(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl
     const int n_partial = (int)std::min<int64_t>(1024, (B * refl_len + 255) / 256);
     const int64_t splits_max = 64;
     const int64_t wmax = std::max<int64_t>(H, refl_len);
-    // workspace: D4 [B][Lg], D0, D1 [B][256], X [B][8], P [splits][wmax][256], loss partials
+    // workspace: D4 [B][Lg], D0, D1 [B][256], X [B][8], P [splits][wmax][256] (also the
+    // column sums' chunk partials, kColsumMaxChunks x wmax), loss partials
+    static_assert(kColsumMaxChunks <= 64 * H, "column-sum partials fit in P");
     const size_t n4 = (size_t)B * refl_len, nh = (size_t)B * H, nx = (size_t)B * 8;
     const size_t np = (size_t)splits_max * wmax * H;
     const size_t need = (n4 + 2 * nh + nx + np + n_partial + 4) * sizeof(float);
@@ -223,7 +225,7 @@ int hrir_mlp_backward(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl
     rc = weight_grad(ctx, gemm_args(refl_len, H, (int)B, D4, 1, refl_len, z3, ld, 1), true, P,
                      grads + L.W4, st);
     if (rc) return rc;
-    HRIR_CUDA_TRY(ctx, launch_colsum(B, refl_len, D4, refl_len, grads + L.b4, st));
+    HRIR_CUDA_TRY(ctx, launch_colsum(B, refl_len, D4, refl_len, P, grads + L.b4, st));
     {
         GemmArgs g = gemm_args(B, H, refl_len, D4, refl_len, 1, params + L.W4, H, 1);
         g.mask = z3;
@@ -240,7 +242,7 @@ int hrir_mlp_backward(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl
     for (int l = 0; l < 2; ++l) {
         rc = weight_grad(ctx, gemm_args(H, H, (int)B, Dc, 1, H, zin[l], ld, 1), true, P, grads + offW[l], st);
         if (rc) return rc;
-        HRIR_CUDA_TRY(ctx, launch_colsum(B, H, Dc, H, grads + offb[l], st));
+        HRIR_CUDA_TRY(ctx, launch_colsum(B, H, Dc, H, P, grads + offb[l], st));
         GemmArgs g = gemm_args(B, H, H, Dc, H, 1, params + offW[l], H, 1);
         g.mask = zmask[l];
         g.ldm = ld;
@@ -253,7 +255,7 @@ int hrir_mlp_backward(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl
     HRIR_CUDA_TRY(ctx, launch_features_layer1((int)B, dirs, params + L.W1, params + L.b1, nullptr, 0, X, st));
     rc = weight_grad(ctx, gemm_args(H, kMlpIn, (int)B, Dc, 1, H, X, 8, 1), false, P, grads + L.W1, st);
     if (rc) return rc;
-    HRIR_CUDA_TRY(ctx, launch_colsum(B, H, Dc, H, grads + L.b1, st));
+    HRIR_CUDA_TRY(ctx, launch_colsum(B, H, Dc, H, P, grads + L.b1, st));
     kt.done();
     return HRIR_OK;
 }

@@ -25,7 +25,7 @@
 // producer warp issues every load, refilling each stage with the unit `stages` ahead as soon
 // as the 20 compute warps have released it.
 // Work is a persistent balanced range of units per CTA; register accumulators are folded
-// every few sources (about 64 products per output) into per-lane FP32 accumulators in shared
+// every few sources (about 128 products per output) into per-lane FP32 accumulators in shared
 // memory, which are flushed every <= 64 sources into partial slots that the reduction sums
 // in a fixed order (two short sums instead of one long one: the FP32 rounding error grows
 // with the square root of a sum's length).

@@ -12,7 +12,8 @@
 //    epilogues: + bias (and softplus into a second output), x [mask > 0] (ReLU'), or a
 //    split-K partial that a second kernel sums in a fixed order (deterministic).
 //  * output_grad_kernel: dz4 = (g - t) / B * sigmoid(z4) and per-block loss partials.
-//  * colsum_kernel: bias gradients, fixed-order column sums.
+//  * colsum_partial_kernel + split_reduce_kernel: bias gradients, column sums over row
+//    chunks, then over the chunks, both in a fixed order.
 //  * adam_kernel: the Adam update with host-computed bias corrections.
 #include "kernels.h"
 
@@ -193,26 +194,52 @@ __global__ void __launch_bounds__(256) output_grad_kernel(int64_t n_rows, int re
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
-// loss = 0.5 * inv_b * sum partial (fixed order)
+// loss = 0.5 * inv_b * sum partial: one warp, lane l sums partials l, l + 32, .. in order
+// (FP64), then a fixed butterfly across the lanes
 __global__ void loss_final_kernel(const float *__restrict__ partial, int n, float inv_b,
                                   float *__restrict__ loss)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < n; ++i) s += partial[i];
-        *loss = (float)(0.5 * inv_b * s);
-    }
+    const int lane = threadIdx.x;
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += partial[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) *loss = (float)(0.5 * inv_b * s);
 }
 
-// out[n] = sum_b D[b][n] (b in order) for n < N
-__global__ void colsum_kernel(int64_t rows, int N, const float *__restrict__ D, int64_t ldd,
-                              float *__restrict__ out)
+// Column sums, first pass: block (x, y) sums rows [y rc, (y + 1) rc) of columns
+// [32 x, 32 x + 32); warp w takes rows w, w + 8, .. of the chunk in order, then the 8 warp sums
+// are added in warp order: P[y][n].  The second pass (split_reduce_kernel with M = 1) adds the
+// chunks in order, so the result does not depend on the launch.
+constexpr int kColsumWarps = 8;
+__global__ void __launch_bounds__(256) colsum_partial_kernel(int64_t rows, int N, const float *__restrict__ D,
+                                                             int64_t ldd, int64_t rc, float *__restrict__ P)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+    __shared__ float red[kColsumWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int n = blockIdx.x * 32 + lane;
+    const int64_t r0 = (int64_t)blockIdx.y * rc;
+    const int64_t r1 = r0 + rc < rows ? r0 + rc : rows;
     float s = 0.f;
-    for (int64_t b = 0; b < rows; ++b) s += D[b * ldd + n];
-    out[n] = s;
+    if (n < N) {
+        int64_t r = r0 + w;
+        // four loads in flight, added in row order
+        for (; r + 3 * kColsumWarps < r1; r += 4 * kColsumWarps) {
+            const float a0 = D[r * ldd + n], a1 = D[(r + kColsumWarps) * ldd + n];
+            const float a2 = D[(r + 2 * kColsumWarps) * ldd + n], a3 = D[(r + 3 * kColsumWarps) * ldd + n];
+            s += a0;
+            s += a1;
+            s += a2;
+            s += a3;
+        }
+        for (; r < r1; r += kColsumWarps) s += D[r * ldd + n];
+    }
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && n < N) {
+        float t = red[0][lane];
+        for (int k = 1; k < kColsumWarps; ++k) t += red[k][lane];
+        P[(int64_t)blockIdx.y * N + n] = t;
+    }
 }
 
 // out[m][n] = sum_z P[z][m][n] (z in order)
@@ -288,10 +315,18 @@ cudaError_t launch_output_grad(int64_t n_rows, int refl_len, const float *g, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_colsum(int64_t rows, int N, const float *D, int64_t ldd, float *out, cudaStream_t st)
+cudaError_t launch_colsum(int64_t rows, int N, const float *D, int64_t ldd, float *P, float *out,
+                          cudaStream_t st)
 {
-    colsum_kernel<<<(N + 127) / 128, 128, 0, st>>>(rows, N, D, ldd, out);
-    return cudaGetLastError();
+    if (N <= 0) return cudaSuccess;
+    int64_t chunks = (rows + 255) / 256;
+    chunks = chunks < 1 ? 1 : (chunks > kColsumMaxChunks ? kColsumMaxChunks : chunks);
+    const int64_t rc = (rows + chunks - 1) / chunks;
+    colsum_partial_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)chunks), 32 * kColsumWarps, 0, st>>>(
+        rows, N, D, ldd, rc, P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_split_reduce((int)chunks, 1, N, P, out, st);
 }
 
 cudaError_t launch_split_reduce(int splits, int M, int N, const float *P, float *out, cudaStream_t st)

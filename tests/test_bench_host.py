@@ -58,7 +58,7 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
 def test_committed_profile_matches_committed_kernel():
     # the headline kernel's ncu summary was taken on the source in the tree
     t = bench.profiled_traffic("mix_sparse_tmem.cu", "mix_sparse_batched_1024x480000_k16.md")
-    assert t == pytest.approx(2.0293e9)
+    assert t == pytest.approx(2.0290e9)
 
 
 def test_traffic_withheld_when_kernel_changed(tmp_path, monkeypatch):
