@@ -60,11 +60,17 @@ GemmArgs gemm_args(int64_t M, int N, int K, const float *A, int64_t sam, int64_t
     return g;
 }
 
-// dW[M][N] = sum_b A(m, b) B(b, n) split over the rows b, partials summed in a fixed order.
+// CTAs a network GEMM should launch to occupy every SM (two per SM)
+int gemm_min_ctas(const hrir_ctx *ctx) { return 2 * std::max(ctx->num_sms, 1); }
+
+// dW[M][N] = sum_b A(m, b) B(b, n) split over the rows b (enough splits to occupy every SM,
+// at most 64), partials summed in a fixed order.
 int weight_grad(hrir_ctx *ctx, GemmArgs g, bool relu_b, float *P, float *out, cudaStream_t st)
 {
     const int64_t rows = g.K;
-    int splits = (int)std::min<int64_t>(64, std::max<int64_t>(1, (rows + 511) / 512));
+    const int64_t tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64);
+    const int64_t want = std::max<int64_t>((rows + 511) / 512, (gemm_min_ctas(ctx) + tiles - 1) / tiles);
+    int splits = (int)std::min<int64_t>(64, std::max<int64_t>(1, want));
     g.k_chunk = (int)round_up((rows + splits - 1) / splits, 16);
     splits = (int)((rows + g.k_chunk - 1) / g.k_chunk);
     g.Z = P;

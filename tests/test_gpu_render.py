@@ -27,40 +27,62 @@ def _dev(a, dtype=None):
 
 
 # ------------------------------------------------------------------------------- top-K pack
-@pytest.mark.parametrize("refl_len", [200, 33, 500, 1000, 2048])
-def test_topk_pack_bit_exact(rend, refl_len):
-    rng = np.random.default_rng(100 + refl_len)
+def _topk_rows(rng, refl_len):
+    """64 x 2 reflection rows with the cases the selection rule has to get right."""
     G = synth.reflection_bank(rng, 64, n_refl=min(60, refl_len), refl_len=refl_len)
     G[0, 0] = 0
     G[1, 1] = -1
     G[2, 0, 5 % refl_len] = np.nan
     G[3, 0] = 0
-    G[3, 0, [7 % refl_len, 3, 11 % refl_len, 2]] = 0.5
+    G[3, 0, [7 % refl_len, 3 % refl_len, 11 % refl_len, 2 % refl_len]] = 0.5
     G[4, 1, :] = 0.25                                  # all equal: the k smallest indices win
     G[5, 0, :] = np.float32(1e-42)                     # denormals are positive
+    G[6, 0, :] = np.float32(np.inf)                    # infinities are the largest values
+    G[6, 1, ::3] = np.float32(0.125)                   # ties at the k-th value
+    G[7, 0, :] = rng.integers(1, 4, refl_len).astype(np.float32)   # few distinct values
+    G[7, 1, : refl_len // 2] = -0.0
+    return G
+
+
+def _check_topk(rend, g, G, k):
+    idx, w, nnz = rend.topk_pack(g, k)
+    torch.cuda.synchronize()
+    ri, rw, rn = oracle.topk(G, k)
+    np.testing.assert_array_equal(nnz.cpu().numpy(), rn)
+    np.testing.assert_array_equal(idx.cpu().numpy().astype(np.int64) & 0xFFFF, ri.astype(np.int64))
+    np.testing.assert_array_equal(w.cpu().numpy().view(np.uint32), rw.view(np.uint32))
+
+
+@pytest.mark.parametrize("refl_len", [200, 4, 36, 128, 256, 33, 500, 1000, 2048])
+def test_topk_pack_bit_exact(rend, refl_len):
+    rng = np.random.default_rng(100 + refl_len)
+    G = _topk_rows(rng, refl_len)
     g = _dev(G)
-    for k in (0, 1, 8, 16, 32, 48, 64):
-        idx, w, nnz = rend.topk_pack(g, k)
-        torch.cuda.synchronize()
-        ri, rw, rn = oracle.topk(G, k)
-        np.testing.assert_array_equal(nnz.cpu().numpy(), rn)
-        np.testing.assert_array_equal(idx.cpu().numpy().astype(np.int64) & 0xFFFF, ri.astype(np.int64))
-        np.testing.assert_array_equal(w.cpu().numpy().view(np.uint32), rw.view(np.uint32))
+    for k in (0, 1, 2, 8, 9, 16, 17, 24, 25, 32, 33, 48, 64, 100, 255):
+        _check_topk(rend, g, G, k)
 
 
-@pytest.mark.parametrize("n_rows,refl_len", [(40000, 200), (20000, 1000)])
-def test_topk_pack_many_rows_bit_exact(rend, n_rows, refl_len):
+@pytest.mark.parametrize("refl_len", [200, 128])
+def test_topk_pack_unaligned_rows_bit_exact(rend, refl_len):
+    """The same rows at an address that is not 16-byte aligned."""
+    rng = np.random.default_rng(7 + refl_len)
+    G = _topk_rows(rng, refl_len)
+    buf = torch.zeros(G.size + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = torch.from_numpy(G.reshape(-1)).cuda()
+    g = buf[1:].view(G.shape)
+    assert g.data_ptr() % 16 != 0
+    for k in (0, 5, 16, 40):
+        _check_topk(rend, g, G, k)
+
+
+@pytest.mark.parametrize("n_rows,refl_len,k", [(40000, 200, 16), (40001, 128, 32), (20000, 1000, 16)])
+def test_topk_pack_many_rows_bit_exact(rend, n_rows, refl_len, k):
     """More rows than one resident wave of warps: every warp walks several rows."""
     rng = np.random.default_rng(n_rows + refl_len)
     G = rng.random((n_rows, refl_len), dtype=np.float32)
     G[rng.random((n_rows, refl_len)) < 0.5] = 0.0
     G[::7, :] = np.float32(0.5)                          # ties everywhere in some rows
-    idx, w, nnz = rend.topk_pack(_dev(G), 16)
-    torch.cuda.synchronize()
-    ri, rw, rn = oracle.topk(G, 16)
-    np.testing.assert_array_equal(nnz.cpu().numpy(), rn)
-    np.testing.assert_array_equal(idx.cpu().numpy().astype(np.int64) & 0xFFFF, ri.astype(np.int64))
-    np.testing.assert_array_equal(w.cpu().numpy().view(np.uint32), rw.view(np.uint32))
+    _check_topk(rend, _dev(G), G, k)
 
 
 # ------------------------------------------------------------------------------ rendering
