@@ -179,8 +179,14 @@ struct GemmArgs {
     const float *mask;
     int64_t ldm;
 };
-cudaError_t launch_gemm(int epi, bool relu_a, bool relu_b, const GemmArgs &g, int splits,
-                        cudaStream_t st);
+// C[m][n] = sum_k A(m, k) B(k, n) over the strides of GemmArgs on the tensor cores, to FP32
+// accuracy (three BF16 terms per operand value), 128-row output tiles; epi: 0 + bias, 1 + bias
+// and softplus into H, 2 x [mask > 0], 3 split-K partial (blockIdx.z); relu_a / relu_b: ReLU
+// on the operand as it is loaded.  A wait that expires ORs DEV_TIMEOUT into *status.
+int gemm_tc_tile_rows();
+int gemm_tc_tile_cols();
+cudaError_t launch_gemm_tc(int epi, bool relu_a, bool relu_b, const GemmArgs &g, int splits, int *status,
+                           cudaStream_t st);
 cudaError_t launch_features_layer1(int n_rows, const float *dirs, const float *W1, const float *b1,
                                    float *z1, int64_t ldz, float *xs, cudaStream_t st);
 cudaError_t launch_output_grad(int64_t n_rows, int refl_len, const float *g, const float *tgt,

@@ -68,14 +68,15 @@ int gemm_min_ctas(const hrir_ctx *ctx) { return 2 * std::max(ctx->num_sms, 1); }
 int weight_grad(hrir_ctx *ctx, GemmArgs g, bool relu_b, float *P, float *out, cudaStream_t st)
 {
     const int64_t rows = g.K;
-    const int64_t tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64);
+    const int64_t tiles = ((g.M + gemm_tc_tile_rows() - 1) / gemm_tc_tile_rows()) *
+                          ((g.N + gemm_tc_tile_cols() - 1) / gemm_tc_tile_cols());
     const int64_t want = std::max<int64_t>((rows + 511) / 512, (gemm_min_ctas(ctx) + tiles - 1) / tiles);
     int splits = (int)std::min<int64_t>(64, std::max<int64_t>(1, want));
     g.k_chunk = (int)round_up((rows + splits - 1) / splits, 16);
     splits = (int)((rows + g.k_chunk - 1) / g.k_chunk);
     g.Z = P;
     g.ldz = g.N;
-    HRIR_CUDA_TRY(ctx, launch_gemm(3, false, relu_b, g, splits, st));
+    HRIR_CUDA_TRY(ctx, launch_gemm_tc(3, false, relu_b, g, splits, ctx->d_status, st));
     HRIR_CUDA_TRY(ctx, launch_split_reduce(splits, (int)g.M, g.N, P, out, st));
     return HRIR_OK;
 }
@@ -128,7 +129,7 @@ int hrir_mlp_forward(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl_
             g.bias = params + (l ? L.b3 : L.b2);
             g.Z = zc + (l + 1) * H;
             g.ldz = ld;
-            HRIR_CUDA_TRY(ctx, launch_gemm(0, true, false, g, 1, st));
+            HRIR_CUDA_TRY(ctx, launch_gemm_tc(0, true, false, g, 1, ctx->d_status, st));
         }
         // output layer: z4 = W4 relu(z3) + b4, g = softplus(z4)
         GemmArgs g = gemm_args(nb, refl_len, H, zc + 2 * H, ld, 1, params + L.W4, 1, H);
@@ -137,7 +138,7 @@ int hrir_mlp_forward(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl_
         g.ldz = ld;
         g.H = out + r0 * refl_len;
         g.ldh = refl_len;
-        HRIR_CUDA_TRY(ctx, launch_gemm(1, true, false, g, 1, st));
+        HRIR_CUDA_TRY(ctx, launch_gemm_tc(1, true, false, g, 1, ctx->d_status, st));
     }
     kt.done();
     return HRIR_OK;
@@ -238,7 +239,7 @@ int hrir_mlp_backward(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl
         g.ldm = ld;
         g.Z = D0;
         g.ldz = H;
-        HRIR_CUDA_TRY(ctx, launch_gemm(2, false, false, g, 1, st));
+        HRIR_CUDA_TRY(ctx, launch_gemm_tc(2, false, false, g, 1, ctx->d_status, st));
     }
     // hidden layers 3 and 2 (dZ in D0 -> weight grads, then dZ of the layer below in D1)
     const float *zin[2] = {z2, z1};
@@ -254,7 +255,7 @@ int hrir_mlp_backward(hrir_ctx *ctx, int64_t n_rows, const float *dirs, int refl
         g.ldm = ld;
         g.Z = Dn;
         g.ldz = H;
-        HRIR_CUDA_TRY(ctx, launch_gemm(2, false, false, g, 1, st));
+        HRIR_CUDA_TRY(ctx, launch_gemm_tc(2, false, false, g, 1, ctx->d_status, st));
         std::swap(Dc, Dn);
     }
     // first layer: its inputs are the features

@@ -1,16 +1,12 @@
 // mlp.cu -- learned reflection filters: the direction -> filter network (5 -> 256 -> 256 ->
 // 256 -> Lg, ReLU, softplus output so every tap is >= 0 like the paper's G >= 0, Eq. 3),
 // its backward pass for the least-squares loss against factorized reflection rows
-// (Algorithm 1 output), and the Adam update.  All FP32.
+// (Algorithm 1 output), and the Adam update.  FP32 values; the matrix products (forward
+// X W^T, backward dZ W, weight gradients dZ^T X) are the tensor-core kernel of
+// mlp_gemm_tc.cu, to FP32 accuracy.
 //
 //  * features_layer1_kernel: x = (sin az, cos az, sin el, cos el, ear) per row, and
 //    z1 = W1 x + b1 (K = 5: one thread per output column, rows staged in shared memory).
-//  * gemm_kernel: C[m][n] = sum_k A(m, k) B(k, n) over arbitrary strides (so the forward
-//    X W^T, the backward dZ W and the weight gradient dZ^T X are one kernel), 64 x 64 tile,
-//    k-step 16, 4 x 4 outputs per thread, optional ReLU on the A or B operand as it is
-//    loaded (layers keep pre-activations z; h = relu(z) is formed on load), and fused
-//    epilogues: + bias (and softplus into a second output), x [mask > 0] (ReLU'), or a
-//    split-K partial that a second kernel sums in a fixed order (deterministic).
 //  * output_grad_kernel: dz4 = (g - t) / B * sigmoid(z4) and per-block loss partials.
 //  * colsum_partial_kernel + split_reduce_kernel: bias gradients, column sums over row
 //    chunks, then over the chunks, both in a fixed order.
@@ -21,105 +17,10 @@ namespace hrir {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
-
-enum Epi : int { EPI_BIAS = 0, EPI_BIAS_SOFTPLUS = 1, EPI_MASK = 2, EPI_PARTIAL = 3 };
-
-__device__ __forceinline__ float softplus_f(float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); }
-
 __device__ __forceinline__ float sigmoid_f(float z)
 {
     const float e = expf(-fabsf(z));
     return z >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
-}
-
-template <int EPI, bool RELU_A, bool RELU_B>
-__global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs g)
-{
-    __shared__ float As[BK][BM + 4];
-    __shared__ float Bs[BK][BN + 4];
-    const int64_t m0 = (int64_t)blockIdx.x * BM;
-    const int n0 = blockIdx.y * BN;
-    const int kb = blockIdx.z * g.k_chunk;
-    const int ke = min(g.K, kb + g.k_chunk);
-    const int t = threadIdx.x;
-    const int tm = (t >> 4) * 4, tn = (t & 15) * 4;
-    float c[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) c[i][j] = 0.f;
-    for (int k0 = kb; k0 < ke; k0 += BK) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int e = t + 256 * i;
-            int kk, mm;
-            if (g.sak == 1) {
-                kk = e & (BK - 1);
-                mm = e >> 4;
-            } else {
-                mm = e & (BM - 1);
-                kk = e >> 6;
-            }
-            const int64_t m = m0 + mm;
-            const int k = k0 + kk;
-            float v = (m < g.M && k < ke) ? g.A[m * g.sam + (int64_t)k * g.sak] : 0.f;
-            if (RELU_A) v = fmaxf(v, 0.f);
-            As[kk][mm] = v;
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int e = t + 256 * i;
-            int kk, nn;
-            if (g.sbn == 1) {
-                nn = e & (BN - 1);
-                kk = e >> 6;
-            } else {
-                kk = e & (BK - 1);
-                nn = e >> 4;
-            }
-            const int n = n0 + nn;
-            const int k = k0 + kk;
-            float v = (n < g.N && k < ke) ? g.B[(int64_t)k * g.sbk + (int64_t)n * g.sbn] : 0.f;
-            if (RELU_B) v = fmaxf(v, 0.f);
-            Bs[kk][nn] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                a[i] = As[kk][tm + i];
-                b[i] = Bs[kk][tn + i];
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) c[i][j] = fmaf(a[i], b[j], c[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t m = m0 + tm + i;
-        if (m >= g.M) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int n = n0 + tn + j;
-            if (n >= g.N) continue;
-            float v = c[i][j];
-            if (EPI == EPI_BIAS || EPI == EPI_BIAS_SOFTPLUS) {
-                v += g.bias[n];
-                g.Z[m * g.ldz + n] = v;
-                if (EPI == EPI_BIAS_SOFTPLUS) g.H[m * g.ldh + n] = softplus_f(v);
-            } else if (EPI == EPI_MASK) {
-                g.Z[m * g.ldz + n] = g.mask[m * g.ldm + n] > 0.f ? v : 0.f;
-            } else {
-                g.Z[((int64_t)blockIdx.z * g.M + m) * g.ldz + n] = v;
-            }
-        }
-    }
 }
 
 // z1[b][n] = b1[n] + sum_k W1[n][k] x_b[k] (skipped when z1 == nullptr); also writes x_b
@@ -269,31 +170,7 @@ __global__ void adam_kernel(int64_t n, float *__restrict__ p, const float *__res
     }
 }
 
-template <int EPI, bool RA, bool RB>
-cudaError_t gemm_t(const GemmArgs &g, int splits, cudaStream_t st)
-{
-    dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN), (unsigned)splits);
-    gemm_kernel<EPI, RA, RB><<<grid, 256, 0, st>>>(g);
-    return cudaGetLastError();
-}
-
 }  // namespace
-
-cudaError_t launch_gemm(int epi, bool relu_a, bool relu_b, const GemmArgs &g, int splits,
-                        cudaStream_t st)
-{
-    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-    if ((g.M + BM - 1) / BM > 0x7fffffff || splits < 1) return cudaErrorInvalidValue;
-#define HRIR_GEMM_CASE(E, A, B)                                                     \
-    if (epi == E && relu_a == A && relu_b == B) return gemm_t<E, A, B>(g, splits, st);
-    HRIR_GEMM_CASE(EPI_BIAS, true, false)
-    HRIR_GEMM_CASE(EPI_BIAS_SOFTPLUS, true, false)
-    HRIR_GEMM_CASE(EPI_MASK, false, false)
-    HRIR_GEMM_CASE(EPI_PARTIAL, false, true)
-    HRIR_GEMM_CASE(EPI_PARTIAL, false, false)
-#undef HRIR_GEMM_CASE
-    return cudaErrorInvalidValue;
-}
 
 cudaError_t launch_features_layer1(int n_rows, const float *dirs, const float *W1, const float *b1,
                                    float *z1, int64_t ldz, float *xs, cudaStream_t st)
