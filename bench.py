@@ -557,6 +557,90 @@ def mode_flops_per_unit(mode, k, n_src):
     return fft_flops_per_unit(n_src)
 
 
+def run_sharded(args):
+    """--shard: the batch's sources split over the ranks (contiguous slices), each rank renders
+    the reflection mix of its slice, the mixes are gathered in rank order (all_gather, the one
+    exchange: 2 x (L + 199) FP32 per rank) and every rank applies the resonance once to their
+    sum (Sec. II linearity).  Strong scaling: every step renders the whole batch."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ranks = Replicas("nccl", device="cuda")
+    rank, world, local = ranks.rank, ranks.world, ranks.local
+    from paper_1502_03162_gb300 import hrir
+    from paper_1502_03162_gb300.shard import render_sharded, shard_range
+    import __graft_entry__
+    __graft_entry__.build()
+    S, L = args.sources, args.length
+    cfg, host = make_inputs(S, L, seed=2, torch=torch)      # the same batch on every rank
+    s0, s1 = shard_range(S, rank, world)
+    rend = hrir.Renderer(local)
+    G = torch.from_numpy(cfg["G"]).cuda()
+    idx, w, nnz = rend.topk_pack(G, K_DEFAULT)
+    idx_h = (idx.cpu().numpy().astype(np.int64) & 0xFFFF).astype(np.uint16)
+    rend.load_filters(idx_h, w.cpu().numpy(), nnz.cpu().numpy(), 200, cfg["res"])
+    host_slice = host[s0:s1]
+    src = host_slice.cuda()
+    dirs_h = torch.from_numpy(cfg["dirs"][s0:s1].copy())
+    dirs = dirs_h.cuda()
+    step = lambda: render_sharded(rend, src, dirs, length=L)  # noqa: E731
+    pk, pk_kind = peaks()
+    with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        rend.kernel_times(reset=True)
+        rend.set_timing(True)
+        clk.mark()
+        ms = time_steps(step, args.steps, 0, torch, ranks.barrier)
+        rend.set_timing(False)
+    kt = rend.kernel_times(reset=True)
+    assert rend.sync() == 0
+    ms = ranks.max_over_ranks(ms)
+    units = S * L * 2                                        # the whole batch, every step
+    kms, kn = kt.get("mix_sparse", (0.0, 0))
+    roof = roofline_of(2.0 * K_DEFAULT * (s1 - s0) * L * 2, (s1 - s0) * L * 4.0, kms / max(kn, 1),
+                       pk, pk_kind)
+    roof["traffic"] = profiled_traffic(*MODE_KERNELS["sparse"][1:])
+    roof["traffic"] = roof["traffic"] * (s1 - s0) / S if roof["traffic"] else None
+    # end to end: this rank's slice from pinned host memory, the sharded render, the output back
+    out_h = torch.empty((2, L + 230), dtype=torch.float32, pin_memory=True)
+
+    def e2e_step():
+        src.copy_(host_slice, non_blocking=True)
+        out_h.copy_(render_sharded(rend, src, dirs, length=L))
+    e2e_step()
+    torch.cuda.synchronize()
+    ranks.barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(2, args.steps // 4)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_ms = ranks.max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps)
+    result = {
+        "metric": METRIC, "value": units / (ms / 1e3), "unit": "source-ear samples/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded AR(1) sources, synthetic 1250-direction filters)",
+        "config": {"workload": WORKLOAD if (S, L) == (S_DEFAULT, L_DEFAULT)
+                   else f"{S} sources x {L} samples AR(1), 1250 directions, K=16 of 200 taps, Lf=32",
+                   "sources": S, "length": L, "k": K_DEFAULT, "refl_len": 200, "res_len": 32,
+                   "mode": "sparse, sharded",
+                   "l2": f"inputs larger than L2 ({S * L * 4 / 1e9:.2f} GB source batch), no flush",
+                   "parallelism": f"source shards x{world} (reflection mixes gathered, resonance once)"},
+        "roofline": roof,
+        "gpu_launches": int(sum(n for _, n in kt.values())),
+        "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in kt.items()},
+        "clocks": clk.summary(),
+        "e2e": {"value": units / (e2e_ms / 1e3), "unit": "source-ear samples/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int((s1 - s0) * host.shape[1] * 4),
+                "d2h_bytes_per_step": int(2 * (L + 230) * 4)},
+    }
+    if rank == 0:
+        print(json.dumps(result))
+    rend.close()
+    ranks.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -570,11 +654,17 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="only the headline path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", action="store_true", help="skip the serving-loop benchmark")
+    ap.add_argument("--shard", action="store_true",
+                    help="split the batch's sources over the ranks (strong scaling) instead of "
+                         "one independent batch per rank")
     ap.add_argument("--learned-sources", type=int, default=4096,
                     help="moving sources of the learned-filter workload (smaller for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.shard:
+        run_sharded(args)
         return
 
     import torch

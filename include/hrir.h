@@ -349,6 +349,32 @@ int hrir_sparsify(hrir_ctx *ctx, int n_dirs, int n_ears, int hrir_len, int refl_
                   int32_t *nnz, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Source sharding.  The render is linear in the sources and the resonance f of Eq. 2 is the
+ * same for all of them (Sec. II), so a batch can be split into disjoint source sets (for
+ * example one per GPU) whose reflection mixes are added once, before f is applied:
+ *     out_e = f_e * sum_c z_{c,e},   z_{c,e} = sum_{s in set c} y_s * g_{d(s),e}.
+ * hrir_render_reflections(..., full, z, z_ld) followed by hrir_apply_resonance(1 part, full)
+ * gives hrir_render_batch(HRIR_SPARSE, full) up to the order of the FP32 sums.
+ *
+ * hrir_render_reflections  The reflection mix z of one source set with the sparse taps alone
+ *                          (the HRIR_SPARSE path without the resonance stage).  Arguments as
+ *                          hrir_render_batch; z device float [2][z_ld], z_len = full ? len +
+ *                          Lg - 1 : len, columns [0, z_len) overwritten.
+ * hrir_apply_resonance     out_e[n] = sum_{l < Lf} f_e[l] z_e[n - l] with z_e = the sum, in part
+ *                          order (compensated), of n_parts >= 1 reflection mixes: z device
+ *                          float [n_parts][2][part_ld], part c ear e at z + (2 c + e) part_ld,
+ *                          z_len samples each (part_ld >= z_len).  out device float [2][out_ld],
+ *                          out_len = full ? z_len + Lf - 1 : z_len.  The FIR is the same
+ *                          compensated dot product as hrir_render_batch's resonance stage.
+ * Both use the filters of hrir_load_filters.
+ * ------------------------------------------------------------------------------------- */
+int hrir_render_reflections(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hrir_dtype dt,
+                            const void *src, const int32_t *dir, int full, float *z, int64_t z_ld,
+                            void *stream);
+int hrir_apply_resonance(hrir_ctx *ctx, int n_parts, int64_t z_len, int64_t part_ld, const float *z,
+                         int full, float *out, int64_t out_ld, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * Rendering precomputed resonance outputs to several direction sets: the order (y * f) * g of
  * Eq. 2.  Given u_{s,e} = y_s * f_e for every source (for example from
  * hrir_resonance_per_source, which the paper's remark on precomputing y * f for sources

@@ -111,6 +111,10 @@ struct ReduceArgs {
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
 // a bounded wait that expires (DEV_TIMEOUT into *status after the wait limit): self-test
 cudaError_t launch_wait_timeout_selftest(int *status, cudaStream_t st);
+// out_e[n] = sum_{l < res_len} res[e][l] z_e[n - l] for n < out_len, z_e[m] = sum over c < n_parts
+// of parts[c][e][m] (parts [n_parts][2][part_ld], m < z_len; compensated, in c order)
+cudaError_t launch_parts_fir(const float *parts, int n_parts, int64_t part_ld, int64_t z_len, const float *res,
+                             int res_len, int64_t out_len, float *out, int64_t out_ld, cudaStream_t st);
 // out[e][0, n) (row stride out_ld) = sum over c of parts[c][e][0, n), in c order
 cudaError_t launch_add_parts(float *out, int64_t out_ld, const float *parts, int n_parts, int64_t n,
                              cudaStream_t st);

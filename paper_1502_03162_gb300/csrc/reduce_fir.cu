@@ -6,6 +6,8 @@
 //              a compensated dot product
 // Each block produces kBlk outputs of one ear: it first forms z for [n0 - Lf + 1, n0 + kBlk)
 // in shared memory (coalesced partial reads, fixed summation order), then applies the FIR.
+// parts_fir_kernel does the same for z given as the sum of a few whole reflection mixes (the
+// mixes of disjoint source sets, e.g. one per GPU), added in part order.
 #include "kernels.h"
 
 namespace hrir {
@@ -16,6 +18,27 @@ constexpr int kBlk = 2048;
 constexpr int kThreads = 256;
 constexpr int kMaxRes = 512;
 constexpr int kMaxSpanTiles = 16;   // partial tiles one block's z span may touch
+
+// sum_l f[l] z[lf - 1 - l] for l < lf: a compensated dot product (Ogita, Rump & Oishi 2005,
+// "Dot2"): the products' and the running sum's rounding errors are carried exactly
+// (error-free transformations) and added at the end, so the result is as accurate as a sum
+// in twice the working precision; the FIR can cancel most of z where f attenuates z's band,
+// which would otherwise magnify its FP32 rounding relative to the output
+__device__ __forceinline__ float fir_dot2(const float *fs, const float *z, int lf)
+{
+    float p = 0.f, c = 0.f;
+    for (int l = 0; l < lf; ++l) {
+        const float x = fs[l], y = z[lf - 1 - l];
+        const float h = __fmul_rn(x, y);
+        const float r = fmaf(x, y, -h);               // h + r == x * y exactly
+        const float s2 = __fadd_rn(p, h);
+        const float bb = __fsub_rn(s2, p);
+        const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(s2, bb)), __fsub_rn(h, bb));  // p + h == s2 + q
+        p = s2;
+        c = __fadd_rn(c, __fadd_rn(q, r));
+    }
+    return __fadd_rn(p, c);
+}
 
 __global__ void __launch_bounds__(kThreads) reduce_fir_kernel(const ReduceArgs a)
 {
@@ -55,23 +78,46 @@ __global__ void __launch_bounds__(kThreads) reduce_fir_kernel(const ReduceArgs a
     for (int i = threadIdx.x; i < kBlk; i += kThreads) {
         const int64_t n = n0 + i;
         if (n >= a.out_len) break;
-        // compensated dot product (Ogita, Rump & Oishi 2005, "Dot2"): the products' and the
-        // running sum's rounding errors are carried exactly (error-free transformations)
-        // and added at the end, so the result is as accurate as a sum in twice the working
-        // precision; the FIR can cancel most of z where f attenuates z's band, which would
-        // otherwise magnify its FP32 rounding relative to the output
-        float p = 0.f, c = 0.f;
-        for (int l = 0; l < lf; ++l) {
-            const float x = fs[l], y = zs[i + lf - 1 - l];
-            const float h = __fmul_rn(x, y);
-            const float r = fmaf(x, y, -h);               // h + r == x * y exactly
-            const float s2 = __fadd_rn(p, h);
-            const float bb = __fsub_rn(s2, p);
-            const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(s2, bb)), __fsub_rn(h, bb));  // p + h == s2 + q
-            p = s2;
-            c = __fadd_rn(c, __fadd_rn(q, r));
+        a.out[e * a.out_ld + n] = fir_dot2(fs, zs + i, lf);
+    }
+}
+
+// Blocks of parts_fir_kernel: out_e[n] = sum_l f_e[l] z_e[n - l], z_e[m] = sum_c parts[c][e][m]
+// (compensated, in c order; zero outside [0, z_len)).
+__global__ void __launch_bounds__(kThreads) parts_fir_kernel(const float *__restrict__ parts, int n_parts,
+                                                             int64_t part_ld, int64_t z_len,
+                                                             const float *__restrict__ res, int res_len,
+                                                             int64_t out_len, float *__restrict__ out,
+                                                             int64_t out_ld)
+{
+    __shared__ float zs[kBlk + kMaxRes - 1];
+    __shared__ float fs[kMaxRes];
+    const int e = blockIdx.y;
+    const int64_t n0 = (int64_t)blockIdx.x * kBlk;
+    const int lf = res ? res_len : 1;
+    const int64_t m_lo = n0 - (lf - 1);
+    for (int l = threadIdx.x; l < lf; l += kThreads) fs[l] = res ? res[e * res_len + l] : 1.0f;
+    const int span = (int)(n0 + kBlk - m_lo);
+    for (int i = threadIdx.x; i < span; i += kThreads) {
+        const int64_t m = m_lo + i;
+        float sum = 0.f;
+        if (m >= 0 && m < z_len) {
+            const float *p = parts + (size_t)e * part_ld + m;
+            float c = 0.f;
+            for (int j = 0; j < n_parts; ++j) {
+                const float y = p[(size_t)j * 2 * part_ld] - c;
+                const float tt = sum + y;
+                c = (tt - sum) - y;
+                sum = tt;
+            }
         }
-        a.out[e * a.out_ld + n] = __fadd_rn(p, c);
+        zs[i] = sum;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBlk; i += kThreads) {
+        const int64_t n = n0 + i;
+        if (n >= out_len) break;
+        out[e * out_ld + n] = fir_dot2(fs, zs + i, lf);
     }
 }
 
@@ -114,6 +160,16 @@ cudaError_t launch_add_parts(float *out, int64_t out_ld, const float *parts, int
     if (n <= 0) return cudaSuccess;
     const int64_t blocks = (2 * n + 255) / 256;
     add_parts_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(out, out_ld, parts, n_parts, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_parts_fir(const float *parts, int n_parts, int64_t part_ld, int64_t z_len, const float *res,
+                             int res_len, int64_t out_len, float *out, int64_t out_ld, cudaStream_t st)
+{
+    if (out_len <= 0) return cudaSuccess;
+    if ((res ? res_len : 1) > kMaxRes || n_parts < 1) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((out_len + kBlk - 1) / kBlk), 2);
+    parts_fir_kernel<<<grid, kThreads, 0, st>>>(parts, n_parts, part_ld, z_len, res, res_len, out_len, out, out_ld);
     return cudaGetLastError();
 }
 

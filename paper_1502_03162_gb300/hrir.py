@@ -63,6 +63,8 @@ SIGNATURES = {
     "hrir_sparsify": ([_vp, _i, _i, _i, _i, _vp, _vp, ctypes.c_float, ctypes.c_float,
                        ctypes.c_float, _vp, _vp, _vp], _i),
     "hrir_render_precomputed": ([_vp, _i, _i64, _i64, _vp, _i, _vp, _i, _vp, _i64, _i64, _vp], _i),
+    "hrir_render_reflections": ([_vp, _i, _i64, _i64, _i, _vp, _vp, _i, _vp, _i64, _vp], _i),
+    "hrir_apply_resonance": ([_vp, _i, _i64, _i64, _vp, _i, _vp, _i64, _vp], _i),
     "hrir_set_timing": ([_vp, _i], _i),
     "hrir_kernel_times": ([_vp, _vp, _vp, _i], _i),
 }
@@ -596,6 +598,55 @@ def hrir_render_precomputed(ctx, u, dirs, full=True, length=None, out=None, stre
     return out[:, :, :out_len]
 
 
+def hrir_render_reflections(ctx, src, dirs, full=True, length=None, z=None, stream=None):
+    """The reflection mix of a source set (sparse taps alone, no resonance).  src: CUDA
+    [S][ld] float32/bfloat16/float16; dirs: CUDA int32 [S].  Returns z: CUDA float32
+    [2][z_len] (or the given buffer), z_len = len + Lg - 1 (full) or len."""
+    import torch
+    _check_tensor(src, "src", cuda=True, dtypes=_src_dtypes(), dim=2, unit_stride=True)
+    S, ld, L = _src_extent(src, length)
+    _check_tensor(dirs, "dirs", cuda=True, dtypes=(torch.int32,), contiguous=True)
+    _require(dirs.numel() >= S, f"dirs: {dirs.numel()} entries for {S} sources")
+    z_len = (L + _refl_len(ctx) - 1 if L > 0 else 0) if full else L
+    if z is None:
+        z = torch.empty((2, max(z_len, 1)), dtype=torch.float32, device=src.device)
+    _check_tensor(z, "z", cuda=True, dtypes=(torch.float32,), min_shape=(2, z_len), unit_stride=True)
+    rc = load_library().hrir_render_reflections(
+        ctx, S, L, ld, _dtype_code(src), src.data_ptr(), dirs.data_ptr(), int(full), z.data_ptr(),
+        z.stride(0), _stream_handle(stream))
+    _check(ctx, rc)
+    return z[:, :z_len]
+
+
+def hrir_apply_resonance(ctx, z, full=True, length=None, out=None, stream=None):
+    """out_e = f_e * sum_c z[c, e] for z: CUDA float32 [n_parts][2][ld] (the reflection mixes of
+    disjoint source sets, added in part order) or [2][ld] (one part); `length` samples of each
+    (default: all).  Returns out: CUDA float32 [2][out_len], out_len = length + Lf - 1 (full)
+    or length."""
+    import torch
+    _check_tensor(z, "z", cuda=True, dtypes=(torch.float32,), unit_stride=True)
+    device = z.device
+    if z.dim() == 2:
+        z = z.unsqueeze(0)
+    _require(z.dim() == 3 and z.shape[1] == 2, f"z: shape {tuple(z.shape)}, expected [n_parts][2][len]")
+    P = z.shape[0]
+    _require(P >= 1, "z: at least one part")
+    _require(P == 1 or z.stride(0) == 2 * z.stride(1),
+             "z: the parts must be [n_parts][2][ld] with the two ears adjacent")
+    Lz = z.shape[2] if length is None else int(length)
+    _require(0 <= Lz <= z.shape[2], f"length {Lz} outside z's {z.shape[2]} samples")
+    out_len = (Lz + _res_len(ctx) - 1 if Lz > 0 else 0) if full else Lz
+    if out is None:
+        out = torch.empty((2, max(out_len, 1)), dtype=torch.float32, device=device)
+    _check_tensor(out, "out", cuda=True, dtypes=(torch.float32,), min_shape=(2, out_len),
+                  unit_stride=True)
+    rc = load_library().hrir_apply_resonance(
+        ctx, P, Lz, z.stride(1), z.data_ptr(), int(full), out.data_ptr(), out.stride(0),
+        _stream_handle(stream))
+    _check(ctx, rc)
+    return out[:, :out_len]
+
+
 _RES_LEN = {}
 _REFL_LEN = {}
 
@@ -646,6 +697,12 @@ class Renderer:
 
     def render(self, src, dirs, mode="sparse", full=True, length=None, out=None, stream=None):
         return hrir_render_batch(self.ctx, src, dirs, mode, full, length, out, stream)
+
+    def render_reflections(self, src, dirs, full=True, length=None, z=None, stream=None):
+        return hrir_render_reflections(self.ctx, src, dirs, full, length, z, stream)
+
+    def apply_resonance(self, z, full=True, length=None, out=None, stream=None):
+        return hrir_apply_resonance(self.ctx, z, full, length, out, stream)
 
     def render_host(self, src, dirs, mode="sparse", full=True, length=None, out=None,
                     stream=None):

@@ -252,3 +252,35 @@ def test_sparsify_and_views_reject(lib, monkeypatch):
     v(fc((S, 2, 1000)), fc((2, S), torch.int32), length=1001)        # longer than u
     v(fc((S, 2, 1000)), fc((2, S), torch.int32), out=fc((2, 2, 1198)))  # output too short
     v(FakeCuda(torch.zeros((2, S, 1000)).transpose(0, 1)), fc((2, S), torch.int32))  # ears apart
+
+
+def test_sharding_calls_valid(lib, monkeypatch):
+    monkeypatch.setitem(hrir._REFL_LEN, CTX, 200)
+    S, L, ld = 37, 30001, 30008
+    z = hrir.hrir_render_reflections(CTX, fc((S, ld)), fc((S,), torch.int32), length=L, stream=0)
+    a = last(lib, "hrir_render_reflections")
+    assert a[1:4] == (S, L, ld) and a[7] == 1 and tuple(z.shape) == (2, L + 199)
+    z0 = hrir.hrir_render_reflections(CTX, fc((S, ld)), fc((S,), torch.int32), full=False, length=L,
+                                      stream=0)
+    assert tuple(z0.shape) == (2, L)
+    parts = fc((3, 2, L + 199))
+    out = hrir.hrir_apply_resonance(CTX, parts, stream=0)
+    a = last(lib, "hrir_apply_resonance")
+    assert a[1:4] == (3, L + 199, L + 199) and tuple(out.shape) == (2, L + 199 + 31)
+    out = hrir.hrir_apply_resonance(CTX, fc((2, L + 199)), full=False, stream=0)   # one part
+    a = last(lib, "hrir_apply_resonance")
+    assert a[1] == 1 and tuple(out.shape) == (2, L + 199)
+
+
+def test_sharding_calls_reject(lib, monkeypatch):
+    monkeypatch.setitem(hrir._REFL_LEN, CTX, 200)
+    r = lambda *a, **k: _rejected(lib, hrir.hrir_render_reflections, CTX, *a, stream=0, **k)  # noqa: E731
+    r(torch.zeros((4, 1000)), fc((4,), torch.int32))                  # host sources
+    r(fc((4, 1000)), fc((3,), torch.int32))                           # too few directions
+    r(fc((4, 1000)), fc((4,), torch.int32), z=fc((2, 1198)))          # z too short
+    ap = lambda *a, **k: _rejected(lib, hrir.hrir_apply_resonance, CTX, *a, stream=0, **k)  # noqa: E731
+    ap(torch.zeros((2, 2, 100)))                                      # host parts
+    ap(fc((2, 3, 100)))                                               # three ears
+    ap(fc((2, 2, 100)), length=101)                                   # longer than the parts
+    ap(fc((2, 2, 100)), out=fc((2, 130)))                             # output too short
+    ap(FakeCuda(torch.zeros((2, 2, 100)).transpose(0, 1)))            # ears not adjacent
