@@ -322,7 +322,34 @@ int hrir_resonance_per_source(hrir_ctx *ctx, int n_src, int64_t len, int64_t src
                               int64_t out_ld, void *stream);
 
 /* ---------------------------------------------------------------------------------------
- * Filter production on the device: the sparsifying fine-tune of Algorithm 1 (Sec. III-D),
+ * Filter production on the device: the factorization x_i = f * g_i of a set of HRIRs
+ * (Eq. 1) by Algorithm 1's alternating minimisation of ||X - F~ G^T||_F^2 (Eq. 3 with
+ * F = F~, the banded Toeplitz matrix of f, Eq. 12), per ear.  Each of `iters` rounds:
+ *   (1) the least-squares resonance for the current G: the normal equations of Eqs. 9-11
+ *       over the Lf free parameters of Eq. 13, A f = b with A[l][l'] = sum_j (G^T G)[j][j + |l
+ *       - l'|] and b[l] = sum_j (X^T G)[j + l][j], solved by Cholesky;
+ *   (2) the multiplicative non-negative update of G (Eq. 4):
+ *       G_ij <- G_ij sqrt(((X F~)+_ij + [G (F~^T F~)-]_ij) / ((X F~)-_ij + [G (F~^T F~)+]_ij)),
+ *       Q+- = (|Q| +- Q) / 2; entries equal to 0 stay 0.
+ *   X      device float [n_dirs][n_ears][M], the HRIRs (rows here), M = hrir_len
+ *   G      device float [n_dirs][n_ears][Lg]: the start on entry (>= 0; Algorithm 1 draws it
+ *          at random, the caller passes it in), the result on return
+ *   f      device float [n_ears][Lf] out, Lf = M - Lg + 1 (1 <= Lf <= 64): the resonance of
+ *          the last round
+ *   trace  device float [n_ears][iters + 1] out (may be NULL): ||X - F~ G^T||_F^2 after the
+ *          first solve with the starting G, then after each round's update
+ *   normalise != 0: f scaled to unit L2 norm and G by the inverse factor (F~ G^T unchanged).
+ * The products (G^T G, X^T G, X F~, G Q+-) run on the tensor cores to FP32 accuracy (each
+ * FP32 value split into three BF16 terms, FP32 accumulation), the Toeplitz sums and the
+ * Cholesky solve in FP64, the residuals from the definition (f * g per row) summed in FP64.
+ * A system that is not positive definite (a G without energy) flags HRIR_EINVAL for
+ * hrir_sync.  1 <= n_ears <= 2, 1 <= Lg <= 1024, iters >= 1; workspace from the context.
+ * ------------------------------------------------------------------------------------- */
+int hrir_factorize(hrir_ctx *ctx, int n_dirs, int n_ears, int hrir_len, int refl_len, const float *X,
+                   float *G, float *f, float *trace, int iters, int normalise, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * The sparsifying fine-tune of Algorithm 1 (Sec. III-D), on the device,
  * so that variable-NNZE tap tables for hrir_load_filters can be made from HRIRs and their
  * factorized resonance without leaving the GPU.  Per direction and ear, with the
  * resonance f fixed (F~ = its banded Toeplitz matrix, Eq. 12):

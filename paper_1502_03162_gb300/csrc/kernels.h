@@ -267,6 +267,28 @@ cudaError_t launch_resonance_gemm(int dtype, const CUtensorMap &tmap, const Reso
                                   int grid, cudaStream_t st);
 
 // ---- filter production: L1-NNLS sparsification, Eq. 14 with D_I or D_W (sparsify.cu) ---------
+// ---- filter production: the alternating minimisation of Algorithm 1 (factorize.cu; its
+// products run on launch_gemm_tc) ----------------------------------------------------------
+constexpr int kFactMaxLf = 64;       // resonance taps the FP64 Toeplitz solve supports
+// a[d] = sum_j P[j][j + d], b[l] = sum_j B[j + l][j] (d, l < Lf), FP64, fixed order
+cudaError_t launch_fact_diag(const float *P, int ldp, const float *B, int ldb, int Lg, int Lf, double *a, double *b,
+                             cudaStream_t st);
+// Toeplitz(a) f = b by FP64 Cholesky; f (FP32) and its autocorrelation r[0, Lf)
+cudaError_t launch_fact_solve(const double *a, const double *b, int Lf, float *f, float *r, int *status,
+                              cudaStream_t st);
+// F~ [M][Lg] of f; Q+ and Q- [Lg][Lg], the positive and negative parts of Toeplitz(r)
+cudaError_t launch_fact_build(const float *f, const float *r, int M, int Lg, int Lf, float *Ft, float *Qp, float *Qm,
+                              cudaStream_t st);
+// the multiplicative update of Eq. 4 on G (rows of stride ldg) from C = X F~, G Q+, G Q-
+cudaError_t launch_fact_update(float *G, int64_t ldg, const float *C, const float *GQp, const float *GQm, int N,
+                               int Lg, cudaStream_t st);
+// *out = ||X - G F~^T||_F^2 (FP64 sums, fixed order); partial: fact_residual_blocks(N) doubles
+int fact_residual_blocks(int N);
+cudaError_t launch_fact_residual(const float *X, int64_t ldx, const float *G, int64_t ldg, const float *f, int N,
+                                 int M, int Lg, int Lf, double *partial, float *out, cudaStream_t st);
+// f <- f / ||f||, G <- G ||f||
+cudaError_t launch_fact_scale(float *f, int Lf, float *G, int64_t ldg, int N, int Lg, cudaStream_t st);
+
 constexpr int kSparsifyMaxLf = 64;   // resonance taps of the fixed f
 struct SparsifyArgs {
     int n_dirs, n_ears, M, Lg, Lf;  // Lf <= kSparsifyMaxLf

@@ -11,16 +11,17 @@
 // below 2^-24 relative), in three accumulators (consecutive MMAs independent) that the
 // epilogue adds.  Each is one tcgen05.mma kind::f16 (M = 128, N = 64 or 32, K = 16).
 //
-// One CTA (8 warps) per 128 x 64 (or 128 x 32) output tile and K range (blockIdx.z: a split of K whose
-// partial products a second kernel sums in a fixed order).  Per k-step of 64 the warps load
+// One CTA (8 warps) per 128 x 64 (or 128 x 32) output tile and K range (blockIdx.z: a split
+// of K whose partial products a second kernel sums in a fixed order).  Per k-step of 64 the warps load
 // A (128 x 64) and B (64 x 64) from global memory with the stride-1 index fastest (coalesced),
 // apply ReLU where the operand is a hidden layer's pre-activation, split, and store the three
 // BF16 planes of each in the canonical no-swizzle K-major layout (8-row x 16-byte core
 // matrices) of one of two shared-memory stages; one thread issues the 24 MMAs of the step and
 // commits them to the stage's mbarrier, and the warps load the next step's operands into
-// registers while they run.  Epilogue: warp (lane quarter q, column half h) reads rows 32 q .. 32 q + 31, columns
-// 32 h .. 32 h + 31 of the accumulator with tcgen05.ld and applies + bias (and softplus into a
-// second output), x [mask > 0] (ReLU'), or writes the split's partial.  Waits are bounded.
+// registers while they run.  Epilogue: warp (lane quarter q, column half h) reads rows
+// 32 q .. 32 q + 31 and its half of the tile's columns from the three accumulators with
+// tcgen05.ld, adds them, and applies + bias (and softplus into a second output), x [mask > 0]
+// (ReLU'), or writes the split's partial.  Waits are bounded.
 #include <cuda_bf16.h>
 
 #include "kernels.h"

@@ -60,6 +60,7 @@ SIGNATURES = {
     "hrir_render_moving": ([_vp, _i, _i64, _i64, _vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _i64,
                             _vp], _i),
     "hrir_resonance_per_source": ([_vp, _i, _i64, _i64, _i, _vp, _i, _vp, _i64, _vp], _i),
+    "hrir_factorize": ([_vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _i, _i, _vp], _i),
     "hrir_sparsify": ([_vp, _i, _i, _i, _i, _vp, _vp, ctypes.c_float, ctypes.c_float,
                        ctypes.c_float, _vp, _vp, _vp], _i),
     "hrir_render_precomputed": ([_vp, _i, _i64, _i64, _vp, _i, _vp, _i, _vp, _i64, _i64, _vp], _i),
@@ -542,6 +543,32 @@ def _filter_rows(X, name="X"):
     _check_tensor(X, name, cuda=True, dtypes=(torch.float32,), dim=3, contiguous=True)
     _require(1 <= X.shape[1] <= 2, f"{name}: {X.shape[1]} ears, expected 1 or 2")
     return X.shape[0], X.shape[1], X.shape[2]
+
+
+def hrir_factorize(ctx, X, G, refl_len: int, iters: int = 50, normalise: bool = True, f=None,
+                   trace=None, stream=None):
+    """Algorithm 1 on the device.  X: CUDA float32 [n_dirs][n_ears][M]; G: CUDA float32
+    [n_dirs][n_ears][Lg], the non-negative start, overwritten with the result.  Returns
+    (f [n_ears][Lf], trace [n_ears][iters + 1]) CUDA tensors."""
+    import torch
+    n_dirs, n_ears, M = _filter_rows(X)
+    Lf = M - int(refl_len) + 1
+    _require(Lf >= 1, f"refl_len {refl_len} longer than the HRIRs ({M})")
+    _require(int(iters) >= 1, f"iters {iters} < 1")
+    _check_tensor(G, "G", cuda=True, dtypes=(torch.float32,), shape=(n_dirs, n_ears, refl_len),
+                  contiguous=True)
+    if f is None:
+        f = torch.empty((n_ears, Lf), dtype=torch.float32, device=X.device)
+    _check_tensor(f, "f", cuda=True, dtypes=(torch.float32,), shape=(n_ears, Lf), contiguous=True)
+    if trace is None:
+        trace = torch.empty((n_ears, int(iters) + 1), dtype=torch.float32, device=X.device)
+    _check_tensor(trace, "trace", cuda=True, dtypes=(torch.float32,), shape=(n_ears, int(iters) + 1),
+                  contiguous=True)
+    rc = load_library().hrir_factorize(ctx, n_dirs, n_ears, M, int(refl_len), X.data_ptr(),
+                                       G.data_ptr(), f.data_ptr(), trace.data_ptr(), int(iters),
+                                       int(normalise), _stream_handle(stream))
+    _check(ctx, rc)
+    return f, trace
 
 
 def hrir_sparsify(ctx, X, f, refl_len: int, lam: float, sigma: float = 0.0, thresh: float = 1e-4,

@@ -284,3 +284,18 @@ def test_sharding_calls_reject(lib, monkeypatch):
     ap(fc((2, 2, 100)), length=101)                                   # longer than the parts
     ap(fc((2, 2, 100)), out=fc((2, 130)))                             # output too short
     ap(FakeCuda(torch.zeros((2, 2, 100)).transpose(0, 1)))            # ears not adjacent
+
+
+def test_factorize_valid_and_reject(lib):
+    X, G = fc((1250, 2, 231)), fc((1250, 2, 200))
+    f, tr = hrir.hrir_factorize(CTX, X, G, 200, iters=50, stream=0)
+    a = last(lib, "hrir_factorize")
+    assert a[1:5] == (1250, 2, 231, 200) and a[9:11] == (50, 1)
+    assert tuple(f.shape) == (2, 32) and tuple(tr.shape) == (2, 51)
+    fa = lambda *a, **k: _rejected(lib, hrir.hrir_factorize, CTX, *a, stream=0, **k)  # noqa: E731
+    fa(torch.zeros((10, 2, 231)), fc((10, 2, 200)), 200)             # host HRIRs
+    fa(fc((10, 2, 231)), fc((10, 2, 199)), 200)                      # G rows
+    fa(fc((10, 2, 231)), fc((10, 2, 200)), 240)                      # Lg > M
+    fa(fc((10, 2, 231)), fc((10, 2, 200)), 200, iters=0)             # no rounds
+    fa(fc((10, 2, 231)), fc((10, 2, 200)), 200, f=fc((2, 31)))       # resonance length
+    fa(fc((10, 2, 231)), fc((10, 2, 200)), 200, iters=5, trace=fc((2, 5)))   # trace length

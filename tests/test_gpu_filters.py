@@ -1,6 +1,6 @@
-"""GPU parity of the filter production (Sec. III-D) against the FP64 oracle: the L1-NNLS
-fine-tune of Algorithm 1 (Eq. 14 with D_I or D_W, hrir_sparsify), and the renderer on the
-variable-NNZE tap tables such fine-tunes produce."""
+"""GPU parity of the filter production (Sec. III) against the FP64 oracle: the alternating
+minimisation of Algorithm 1 (hrir_factorize), its L1-NNLS fine-tune (Eq. 14 with D_I or D_W,
+hrir_sparsify), and the renderer on the variable-NNZE tap tables they produce."""
 import numpy as np
 import pytest
 
@@ -34,6 +34,63 @@ def hset():
 
 def _cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_one_round_matches_oracle(rend, hset):
+    """From the same starting G: the resonance solve (Eqs. 9-11), the update of G (Eq. 4) and
+    both residuals of the first round (Algorithm 1).  The products are FP32-accurate (sums of
+    up to 1250 terms accumulated in FP32), the Toeplitz sums, the solve and the residuals
+    FP64: f, G and the trace agree with the FP64 oracle to a few 1e-7 relative."""
+    from paper_1502_03162_gb300 import hrir
+    X, _, _, _ = hset
+    N = X.shape[0]
+    rng = np.random.default_rng(5)
+    G0 = rng.random((N, 2, LG), dtype=np.float32)
+    G0[rng.random(G0.shape) < 0.3] = 0.0          # zeros stay zero
+    Gd = _cuda(G0)
+    f, tr = hrir.hrir_factorize(rend.ctx, _cuda(X), Gd, LG, iters=1, normalise=False)
+    assert rend.sync() == 0
+    f, tr, G1 = f.cpu().numpy(), tr.cpu().numpy(), Gd.cpu().numpy()
+    for e in range(2):
+        Xe = X[:, e, :].T.astype(np.float64)
+        Ge = G0[:, e, :].astype(np.float64)
+        f0 = fz.solve_resonance(Xe, Ge, 32)
+        ref = fz.update_reflections(Xe, fz.toeplitz_filter_matrix(f0, LG), Ge)
+        df_ = np.abs(f[e] - f0).max() / np.abs(f0).max()
+        dG = np.abs(G1[:, e] - ref).max() / ref.max()
+        r0, r1 = fz.residual(Xe, f0, Ge), fz.residual(Xe, f0, ref)
+        dtr = np.abs(tr[e] / [r0, r1] - 1).max()
+        print(f"FACTORIZE one round ear {e}: f {df_:.2e}, G {dG:.2e}, trace {dtr:.2e}")
+        assert np.all(G1[:, e][Ge == 0] == 0)
+        assert df_ <= 1e-5 and dG <= 1e-5 and dtr <= 1e-5
+
+
+def test_fifty_rounds_track_the_oracle(rend, hset):
+    """Algorithm 1 with the paper's 50 rounds from the same random start: the residual trace
+    does not increase (the exact resonance solve and Eq. 4 never increase it), follows the
+    FP64 trace, and the normalised resonance and the reconstruction f * g agree."""
+    from paper_1502_03162_gb300 import hrir
+    X, _, _, _ = hset
+    N = X.shape[0]
+    rng = np.random.default_rng(6)
+    G0 = rng.random((N, 2, LG), dtype=np.float32)
+    Gd = _cuda(G0)
+    f, tr = hrir.hrir_factorize(rend.ctx, _cuda(X), Gd, LG, iters=50, normalise=True)
+    assert rend.sync() == 0
+    f, tr, G = f.cpu().numpy(), tr.cpu().numpy(), Gd.cpu().numpy()
+    for e in range(2):
+        Xe = X[:, e, :].T.astype(np.float64)
+        fo, Go, tro = fz.factorize(Xe, LG, G0[:, e, :].astype(np.float64), iters=50)
+        dtr = np.abs(tr[e] / tro - 1).max()
+        df_ = np.abs(f[e] - fo).max() / np.abs(fo).max()
+        rec = np.stack([np.convolve(f[e].astype(np.float64), g) for g in G[:, e].astype(np.float64)])
+        reco = (fz.toeplitz_filter_matrix(fo, LG) @ Go.T).T
+        drec = np.abs(rec - reco).max() / np.abs(reco).max()
+        print(f"FACTORIZE 50 rounds ear {e}: trace {dtr:.2e}, f {df_:.2e}, f*g {drec:.2e}, "
+              f"residual {tro[0]:.4e} -> {tro[-1]:.4e}")
+        assert np.all(np.diff(tr[e]) <= 1e-5 * tr[e][0]), "GPU residual trace increased"
+        assert dtr <= 1e-4 and df_ <= 1e-4 and drec <= 1e-4
+        assert abs(np.linalg.norm(f[e].astype(np.float64)) - 1.0) < 1e-5
 
 
 @pytest.mark.parametrize("lam,sigma", [(0.0, 0.0), (1e-3, 0.0), (1e-3, 60.0), (1e-2, 0.0)])
@@ -142,3 +199,30 @@ def test_fine_tune_on_the_device_feeds_the_renderer(rend, hset):
     o = rend.render(_cuda(y), _cuda(dirs)).cpu().numpy()
     assert rend.sync() == 0
     assert_close(o, oracle.render_sparse(y, dirs, idx, w, nn, LG, f), what="device fine-tuned tables")
+
+
+def test_device_factorization_feeds_the_fine_tune_and_the_renderer(rend, hset):
+    """Filters made entirely on the device: Algorithm 1 (hrir_factorize, 50 rounds) -> the
+    L1-NNLS fine-tune at lambda = 1e-3 (hrir_sparsify) -> tap tables (hrir_topk_pack keeping
+    every non-zero) -> render, against the oracle's mix on the same tables."""
+    from paper_1502_03162_gb300 import hrir
+    X, _, _, _ = hset
+    N = X.shape[0]
+    rng = np.random.default_rng(10)
+    Gd = _cuda(rng.random((N, 2, LG), dtype=np.float32))
+    Xd = _cuda(X)
+    f, _ = hrir.hrir_factorize(rend.ctx, Xd, Gd, LG, iters=50)
+    Gs, nnz = hrir.hrir_sparsify(rend.ctx, Xd, f, LG, 1e-3, 0.0, 1e-4)
+    k = int(nnz.max().item())
+    idx_d, w_d, nnz_d = rend.topk_pack(Gs, k)
+    assert rend.sync() == 0
+    idx = (idx_d.cpu().numpy().astype(np.int64) & 0xFFFF).astype(np.uint16)
+    w, nn, fh = w_d.cpu().numpy(), nnz_d.cpu().numpy(), f.cpu().numpy()
+    print(f"FILTERS from the device factorization: mean NNZE {nn.mean():.2f} (max {k})")
+    S, L = 64, 20000
+    y = synth.sources_ar1(rng, S, L)
+    dirs = synth.directions(rng, S, N)
+    rend.load_filters(idx, w, nn, LG, fh)
+    o = rend.render(_cuda(y), _cuda(dirs)).cpu().numpy()
+    assert rend.sync() == 0
+    assert_close(o, oracle.render_sparse(y, dirs, idx, w, nn, LG, fh), what="device-made filters")
