@@ -80,8 +80,9 @@ const char *hrir_last_error(const hrir_ctx *ctx);
 
 /* Wait for all work enqueued on `stream`, then return and clear any device-side error flag:
  * HRIR_EINVAL (a direction id was out of range, that source rendered as silence, a
- * device tap table of hrir_render_moving held an invalid entry, which was ignored, or an
- * hrir_sparsify row hit the solver's limits),
+ * device tap table of hrir_render_moving held an invalid entry, which was ignored, an
+ * hrir_sparsify row hit the solver's limits, or an hrir_factorize resonance system was not
+ * positive definite),
  * HRIR_ETIMEDOUT (a bounded wait expired; the output of that call is incomplete), or
  * HRIR_ECUDA if the stream reported a CUDA error. */
 int hrir_sync(hrir_ctx *ctx, void *stream);

@@ -13,7 +13,7 @@ enum : int {
     DEV_BAD_DIR = 1,    // a direction id was out of range (source rendered as silence)
     DEV_TIMEOUT = 2,    // a bounded mbarrier wait expired; the kernel returned early
     DEV_BAD_TAP = 4,    // a device tap table held an index >= Lg or a count > k_max (ignored)
-    DEV_SOLVER = 8,     // an L1-NNLS row hit the solver's support or iteration limit
+    DEV_SOLVER = 8,     // an L1-NNLS row hit the solver's limits, or a resonance system was not SPD
 };
 
 // Bounded waits give up after this many nanoseconds of %globaltimer.

@@ -449,8 +449,10 @@ int hrir_sync(hrir_ctx *ctx, void *stream)
     if (st & DEV_BAD_TAP)
         return fail(ctx, HRIR_EINVAL, "a device tap table held an index >= Lg or a count > k_max (ignored)");
     if (st & DEV_SOLVER)
-        return fail(ctx, HRIR_EINVAL, "an L1-NNLS row outgrew the solver's support limit or iteration "
-                                      "limit (its result is the last feasible iterate)");
+        return fail(ctx, HRIR_EINVAL, "a filter-production solve failed: an L1-NNLS row outgrew the "
+                                      "solver's support or iteration limit (its result is the last "
+                                      "feasible iterate), or a resonance system of hrir_factorize was "
+                                      "not positive definite");
     return fail(ctx, HRIR_EINVAL, "a direction id was out of range (rendered as silence)");
 }
 
