@@ -9,7 +9,7 @@
 //        a[d] = sum_j P[j][j + d]   (d < Lf; A[l][l'] = a[|l - l'|], symmetric Toeplitz)
 //        b[l] = sum_j B[j + l][j]   (l < Lf)
 //    each a fixed-order sum in FP64.
-//  * fact_solve_kernel: A f = b by Cholesky in FP64 (one thread; Lf <= 64), f rounded to
+//  * fact_solve_kernel: A f = b by Cholesky in FP64 (one CTA; Lf <= 64), f rounded to
 //    FP32, and its autocorrelation r[d] = sum_l f[l] f[l + d] (FP64 sums of the FP32 taps),
 //    which gives F~^T F~ = Toeplitz(r) (every column of F~ holds the whole of f).
 //  * fact_build_kernel: F~ (M x Lg) and Q+ = max(F~^T F~, 0), Q- = max(-F~^T F~, 0) (Lg x Lg).
@@ -17,9 +17,10 @@
 //        G_ij <- G_ij sqrt( (C+_ij + [G Q-]_ij) / (C-_ij + [G Q+]_ij) ),  C = X F~,
 //    C+- = (|C| +- C) / 2; entries equal to 0 stay 0 (the denominator is >= G_ij r[0] > 0).
 //  * fact_residual_kernel + fact_residual_sum_kernel: ||X - G F~^T||_F^2 straight from the
-//    definition (the convolution f * g_i per row, differences squared and summed in FP64,
-//    partials added in a fixed order).
+//    definition (the convolution f * g_i per row in double-float, the differences squared and
+//    summed in FP64, partials added in a fixed order).
 //  * fact_scale_kernel: the final normalisation f <- f / ||f||, G <- G ||f||.
+#include "dfloat.cuh"
 #include "kernels.h"
 
 namespace hrir {
@@ -65,42 +66,66 @@ __global__ void __launch_bounds__(kThreads) fact_diag_kernel(const float *__rest
     }
 }
 
-// one thread: Cholesky of the Lf x Lf Toeplitz system in FP64, f (FP32) and r
-__global__ void fact_solve_kernel(const double *__restrict__ a, const double *__restrict__ b, int Lf,
-                                  float *__restrict__ f, float *__restrict__ r, int *status)
+// Cholesky of the Lf x Lf Toeplitz system in FP64 by one CTA of kSolveThreads: right-looking
+// (column k scaled in parallel, then the trailing matrix updated in parallel), the two
+// triangular solves one row at a time with the later right-hand sides updated in parallel;
+// f rounded to FP32 and its autocorrelation r (thread d: r[d])
+constexpr int kSolveThreads = 64;
+__global__ void __launch_bounds__(kSolveThreads) fact_solve_kernel(const double *__restrict__ a,
+                                                                   const double *__restrict__ b, int Lf,
+                                                                   float *__restrict__ f, float *__restrict__ r,
+                                                                   int *status)
 {
-    __shared__ double L[kFactMaxLf * kFactMaxLf];
+    __shared__ double A[kFactMaxLf * kFactMaxLf];   // becomes L (lower triangle)
     __shared__ double z[kFactMaxLf];
-    if (threadIdx.x != 0) return;
-    for (int i = 0; i < Lf; ++i) {
-        for (int j = 0; j <= i; ++j) {
-            double s = a[i - j];
-            for (int k = 0; k < j; ++k) s -= L[i * Lf + k] * L[j * Lf + k];
-            if (i == j) {
-                if (!(s > 0.0)) {                  // not positive definite: G carries no energy
-                    atomicOr(status, DEV_SOLVER);
-                    s = 1e-300;
-                }
-                L[i * Lf + i] = sqrt(s);
-            } else {
-                L[i * Lf + j] = s / L[j * Lf + j];
+    __shared__ float fs[kFactMaxLf];
+    const int tid = threadIdx.x, n2 = Lf * Lf;
+    for (int q = tid; q < n2; q += kSolveThreads) {
+        const int i = q / Lf, j = q - i * Lf;
+        A[q] = a[i > j ? i - j : j - i];
+    }
+    for (int i = tid; i < Lf; i += kSolveThreads) z[i] = b[i];
+    __syncthreads();
+    for (int k = 0; k < Lf; ++k) {
+        if (tid == 0) {
+            double d = A[k * Lf + k];
+            if (!(d > 0.0)) {                          // not positive definite: G carries no energy
+                atomicOr(status, DEV_SOLVER);
+                d = 1e-300;
             }
+            A[k * Lf + k] = sqrt(d);
         }
+        __syncthreads();
+        const double dk = A[k * Lf + k];
+        for (int i = k + 1 + tid; i < Lf; i += kSolveThreads) A[i * Lf + k] /= dk;
+        __syncthreads();
+        const int m = Lf - k - 1;                      // trailing (m x m), lower triangle used
+        for (int q = tid; q < m * m; q += kSolveThreads) {
+            const int i = k + 1 + q / m, j = k + 1 + q % m;
+            if (j <= i) A[i * Lf + j] -= A[i * Lf + k] * A[j * Lf + k];
+        }
+        __syncthreads();
     }
-    for (int i = 0; i < Lf; ++i) {                 // L z = b
-        double s = b[i];
-        for (int k = 0; k < i; ++k) s -= L[i * Lf + k] * z[k];
-        z[i] = s / L[i * Lf + i];
+    for (int i = 0; i < Lf; ++i) {                     // L z = b
+        if (tid == 0) z[i] /= A[i * Lf + i];
+        __syncthreads();
+        for (int j = i + 1 + tid; j < Lf; j += kSolveThreads) z[j] -= A[j * Lf + i] * z[i];
+        __syncthreads();
     }
-    for (int i = Lf - 1; i >= 0; --i) {            // L^T f = z
-        double s = z[i];
-        for (int k = i + 1; k < Lf; ++k) s -= L[k * Lf + i] * z[k];
-        z[i] = s / L[i * Lf + i];
+    for (int i = Lf - 1; i >= 0; --i) {                // L^T f = z
+        if (tid == 0) z[i] /= A[i * Lf + i];
+        __syncthreads();
+        for (int j = tid; j < i; j += kSolveThreads) z[j] -= A[i * Lf + j] * z[i];
+        __syncthreads();
     }
-    for (int i = 0; i < Lf; ++i) f[i] = (float)z[i];
-    for (int d = 0; d < Lf; ++d) {
+    for (int i = tid; i < Lf; i += kSolveThreads) {
+        fs[i] = (float)z[i];
+        f[i] = fs[i];
+    }
+    __syncthreads();
+    for (int d = tid; d < Lf; d += kSolveThreads) {
         double s = 0.0;
-        for (int l = 0; l + d < Lf; ++l) s += (double)f[l] * (double)f[l + d];
+        for (int l = 0; l + d < Lf; ++l) s += (double)fs[l] * (double)fs[l + d];
         r[d] = (float)s;
     }
 }
@@ -165,10 +190,11 @@ __global__ void __launch_bounds__(kThreads) fact_residual_kernel(const float *__
         const float *g = G + (int64_t)i * ldg;
         const int l0 = m - (Lg - 1) > 0 ? m - (Lg - 1) : 0;
         const int l1 = m < Lf - 1 ? m : Lf - 1;
-        double rec = 0.0;
-        for (int l = l0; l <= l1; ++l) rec += (double)fs[l] * (double)g[m - l];
-        const double d = (double)X[(int64_t)i * ldx + m] - rec;
-        s += d * d;
+        dfl rec = df_make(0.f);                   // (f * g_i)[m] in double-float
+        for (int l = l0; l <= l1; ++l) rec = df_fma(rec, fs[l], g[m - l]);
+        const dfl d = df_add(df_make(X[(int64_t)i * ldx + m]), df_neg(rec));
+        const double dd = (double)d.hi + (double)d.lo;
+        s += dd * dd;
     }
     s = block_sum(s, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -224,7 +250,7 @@ cudaError_t launch_fact_solve(const double *a, const double *b, int Lf, float *f
                               cudaStream_t st)
 {
     if (Lf < 1 || Lf > kFactMaxLf) return cudaErrorInvalidValue;
-    fact_solve_kernel<<<1, 32, 0, st>>>(a, b, Lf, f, r, status);
+    fact_solve_kernel<<<1, kSolveThreads, 0, st>>>(a, b, Lf, f, r, status);
     return cudaGetLastError();
 }
 
