@@ -85,6 +85,10 @@ int make_source_map(hrir_ctx *ctx, CUtensorMap *m, const void *src, int dt, int6
 // when len < kMixBox there are no full rows and *m is a copy of the 2-D map `fallback`.
 int make_source_map3(hrir_ctx *ctx, CUtensorMap *m, const CUtensorMap &fallback, const void *src,
                      int dt, int64_t len, int64_t ld, int n_src, int box_rows);
+// 3-D view {32, rows, n_src} of FP32 sources (rows of 32 samples, row stride 128 bytes, source
+// stride ld), box {32, box_rows, 1}, 128-byte swizzle, zero fill outside
+int make_source_rows32_map(hrir_ctx *ctx, CUtensorMap *m, const float *src, int64_t rows, int64_t ld, int n_src,
+                           int box_rows);
 cudaEvent_t take_event(hrir_ctx *ctx);
 
 // Brackets one kernel launch with events when timing is enabled.

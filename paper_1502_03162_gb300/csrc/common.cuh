@@ -14,6 +14,7 @@ enum : int {
     DEV_TIMEOUT = 2,    // a bounded mbarrier wait expired; the kernel returned early
     DEV_BAD_TAP = 4,    // a device tap table held an index >= Lg or a count > k_max (ignored)
     DEV_SOLVER = 8,     // an L1-NNLS row hit the solver's limits, or a resonance system was not SPD
+    DEV_LAYOUT = 16,    // a kernel found its shared memory misaligned for its TMA layout (did nothing)
 };
 
 // Bounded waits give up after this many nanoseconds of %globaltimer.

@@ -168,6 +168,22 @@ int make_source_map3(hrir_ctx *ctx, CUtensorMap *m, const CUtensorMap &fallback,
     return HRIR_OK;
 }
 
+int make_source_rows32_map(hrir_ctx *ctx, CUtensorMap *m, const float *src, int64_t rows, int64_t ld, int n_src,
+                           int box_rows)
+{
+    auto fn = tensor_map_encoder();
+    if (!fn) return fail(ctx, HRIR_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    const cuuint64_t dims[3] = {32, (cuuint64_t)rows, (cuuint64_t)n_src};
+    const cuuint64_t strides[2] = {32 * 4, (cuuint64_t)(ld * 4)};
+    const cuuint32_t box[3] = {32, (cuuint32_t)box_rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(src), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, HRIR_ECUDA, "cuTensorMapEncodeTiled (32-sample rows) failed (%d)", (int)r);
+    return HRIR_OK;
+}
+
 cudaEvent_t take_event(hrir_ctx *ctx)
 {
     if (!ctx->free_events.empty()) {
@@ -448,6 +464,9 @@ int hrir_sync(hrir_ctx *ctx, void *stream)
         return fail(ctx, HRIR_ETIMEDOUT, "a bounded device wait expired (output incomplete)");
     if (st & DEV_BAD_TAP)
         return fail(ctx, HRIR_EINVAL, "a device tap table held an index >= Lg or a count > k_max (ignored)");
+    if (st & DEV_LAYOUT)
+        return fail(ctx, HRIR_ECUDA, "a kernel found its shared memory misaligned for its TMA layout "
+                                     "(the call produced no output)");
     if (st & DEV_SOLVER)
         return fail(ctx, HRIR_EINVAL, "a filter-production solve failed: an L1-NNLS row outgrew the "
                                       "solver's support or iteration limit (its result is the last "

@@ -249,6 +249,39 @@ size_t moving_smem_bytes(int halo, int n_js, int k_max);
 cudaError_t launch_moving_mix(const MovingArgs &a, int grid, size_t smem, cudaStream_t st);
 int moving_ctas_per_sm(size_t smem);   // resident CTAs per SM (>= 1)
 
+// ---- moving sources on tensor-memory windows (moving_tmem.cu) -------------------------------
+// 128 TMEM lanes x 32 outputs: a 4096-output tile; a lane never straddles a segment
+// (seg_len % 32 == 0).  Each lane's window of 256 samples (224 filter offsets + its 32
+// outputs) double-buffered in the 512 TMEM columns; the source tile (4096 + 256 samples)
+// arrives by a 3-D TMA load of 32-sample rows with the 128-byte swizzle, so that the copy
+// into TMEM reads shared memory without bank conflicts.
+constexpr int kMvR = 32, kMvTile = 128 * kMvR, kMvCols = 256, kMvSpan = kMvCols - kMvR;   // 224
+constexpr int kMvHalo = 256, kMvBufElems = kMvTile + kMvHalo;   // 4352 samples, 136 rows of 32
+constexpr int kMvSegQ = 4;        // segments one lane quarter (1024 outputs) spans, seg_len >= 256
+constexpr int kMvMaxK = 16;       // taps per (segment, ear) table row
+constexpr int kMvMaxU = 5 * kMvMaxK;   // union of the quarter's <= 5 tables
+constexpr int kMvMaxTableSegs = kMvTile / 256 + 2;   // table rows staged per unit
+struct MovingTmemArgs {
+    const float *src;            // [n_src][ld], ld >= round_up(len, 32)
+    int64_t ld, len;
+    int n_src, n_seg, seg_len, k_max;   // tables [n_src][n_seg][2][k_max], k_max % 4 == 0
+    const uint16_t *tap_idx;
+    const float *tap_w;
+    const uint8_t *tap_nnz;      // [n_src][n_seg][2]
+    int refl_len;                // <= kMvSpan
+    int rows;                    // ceil(len / 32): rows of the 3-D source view
+    int stages, fold;
+    int runacc_off, prog_off;    // shared-memory offsets of the fold accumulators, programs
+    Partition part;
+    float *partial;              // [n_tiles][slots][2][kMvTile]
+    int slots;
+    int *status;
+};
+// shared memory of the pipeline with `stages` stages (0 when it does not fit)
+size_t moving_tmem_smem_bytes(int stages, int k_max, int *runacc_off, int *prog_off);
+cudaError_t launch_moving_tmem(const CUtensorMap &tmap3, const MovingTmemArgs &a, int grid, size_t smem,
+                               cudaStream_t st);
+
 // ---- per-source resonance as a Toeplitz-block GEMM on the tensor cores ----------------------
 constexpr int kResTile = 4096;   // outputs per MMA tile (128 blocks of 32)
 constexpr int kResMaxLf = 32;    // resonance taps one block row covers

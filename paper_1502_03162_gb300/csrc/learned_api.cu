@@ -81,6 +81,75 @@ int weight_grad(hrir_ctx *ctx, GemmArgs g, bool relu_b, float *P, float *out, cu
     return HRIR_OK;
 }
 
+// The moving-source mix on tensor-memory windows, then the reduction with the resonance.
+int render_moving_tmem(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, const float *src, int n_seg,
+                       int seg_len, int k_max, const uint16_t *tap_idx, const float *tap_w, const uint8_t *tap_nnz,
+                       int64_t mix_len, int64_t out_len, float *out, int64_t out_ld, cudaStream_t st)
+{
+    const int n_tiles = (int)((mix_len + kMvTile - 1) / kMvTile);
+    int stages = kMixMaxStages, runacc_off = 0, prog_off = 0;
+    size_t smem = 0;
+    for (; stages >= 2; --stages)
+        if ((smem = moving_tmem_smem_bytes(stages, k_max, &runacc_off, &prog_off)) != 0) break;
+    if (stages < 2) return fail(ctx, HRIR_EINVAL, "the moving-source pipeline does not fit in shared memory");
+    Partition part;
+    part.U = (int64_t)n_tiles * n_src;
+    part.P = std::min<int64_t>(ctx->num_sms, part.U);
+    part.n_src = n_src;
+    part.gs = kRunSources;
+    int slots = 0;
+    for (int t = 0; t < n_tiles; ++t) slots = std::max(slots, part.slots(t));
+    const size_t pbytes = (size_t)n_tiles * slots * 2 * kMvTile * sizeof(float);
+    int rc = grow(ctx, (void **)&ctx->d_partial, &ctx->partial_bytes, pbytes);
+    if (rc) return rc;
+    CUtensorMap tmap3;
+    rc = make_source_rows32_map(ctx, &tmap3, src, len / 32, src_ld, n_src, kMvBufElems / 32);
+    if (rc) return rc;
+    MovingTmemArgs a{};
+    a.src = src;
+    a.ld = src_ld;
+    a.len = len;
+    a.n_src = n_src;
+    a.n_seg = n_seg;
+    a.seg_len = seg_len;
+    a.k_max = k_max;
+    a.tap_idx = tap_idx;
+    a.tap_w = tap_w;
+    a.tap_nnz = tap_nnz;
+    a.refl_len = ctx->refl_len;
+    a.rows = (int)(len / 32);
+    a.stages = stages;
+    a.fold = std::max(1, kFoldTerms / k_max);
+    a.runacc_off = runacc_off;
+    a.prog_off = prog_off;
+    a.part = part;
+    a.partial = ctx->d_partial;
+    a.slots = slots;
+    a.status = ctx->d_status;
+    {
+        KernelTimer kt(ctx, HRIR_K_MOVING, st);
+        HRIR_CUDA_TRY(ctx, launch_moving_tmem(tmap3, a, (int)part.P, smem, st));
+        kt.done();
+    }
+    ReduceArgs r;
+    r.partial = ctx->d_partial;
+    r.slots = slots;
+    r.n_tiles = n_tiles;
+    r.tile = kMvTile;
+    r.part = part;
+    r.res = ctx->d_res;
+    r.res_len = ctx->res_len;
+    r.out_len = out_len;
+    r.out = out;
+    r.out_ld = out_ld;
+    {
+        KernelTimer kt(ctx, HRIR_K_REDUCE, st);
+        HRIR_CUDA_TRY(ctx, launch_reduce(r, st));
+        kt.done();
+    }
+    return HRIR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -311,6 +380,13 @@ int hrir_render_moving(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, co
     if (src_ld < len || ((uintptr_t)src % 16) || (src_ld % 4))
         return fail(ctx, HRIR_EINVAL, "src must be 16-byte aligned with src_ld >= len, src_ld %% 4 == 0");
     const int64_t mix_len = std::min<int64_t>(out_len, len + ctx->refl_len - 1);
+    // tensor-memory windows (moving_tmem.cu) where their shape rules hold: whole 32-sample rows
+    // (len % 32 == 0), segments of >= 256 samples, <= 16 taps a row in 16-byte table rows,
+    // reflection filters within the 224-offset window
+    if (seg_len >= 256 && seg_len % 32 == 0 && k_max % 4 == 0 && k_max <= kMvMaxK && ctx->refl_len <= kMvSpan &&
+        len % 32 == 0 && len > 0 && ((uintptr_t)tap_idx % 16) == 0 && ((uintptr_t)tap_w % 16) == 0)
+        return render_moving_tmem(ctx, n_src, len, src_ld, src, n_seg, seg_len, k_max, tap_idx, tap_w, tap_nnz,
+                                  mix_len, out_len, out, out_ld, st);
     const int n_tiles = (int)((mix_len + kMovTile - 1) / kMovTile);
     const int halo = (int)round_up(ctx->refl_len, 4);
     const int n_js = (kMovTile + seg_len - 1) / seg_len + 2;

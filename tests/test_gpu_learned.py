@@ -134,7 +134,13 @@ def _moving_case(rng, S, L, seg, k, n_dirs=40):
 @pytest.mark.parametrize("S,L,seg,k", [(5, 3000, 256, 16), (3, 1000, 128, 8), (70, 20001, 256, 16),
                                        (2, 5000, 1024, 32), (1, 100, 256, 16),
                                        # k_max not a multiple of 4: tables staged by lane copies
-                                       (4, 2999, 128, 6), (2, 1537, 640, 5)])
+                                       (4, 2999, 128, 6), (2, 1537, 640, 5),
+                                       # tensor-memory windows (len % 32 == 0, seg_len >= 256,
+                                       # k_max % 4 == 0 and <= 16): several tiles and units, a
+                                       # segment length that does not divide a lane quarter,
+                                       # one 32-sample row, the benchmark's length
+                                       (5, 3072, 256, 16), (70, 20000, 256, 16), (3, 12288, 512, 8),
+                                       (9, 6400, 384, 12), (1, 32, 256, 16), (2, 96000, 256, 16)])
 def test_moving_render_matches_oracle(rend, S, L, seg, k):
     from paper_1502_03162_gb300 import hrir
     rng = np.random.default_rng(S * 31 + L)
@@ -153,20 +159,21 @@ def test_moving_render_matches_oracle(rend, S, L, seg, k):
         assert_close(o, ref[:, :o.shape[1]], what=f"moving S={S} L={L} seg={seg} full={full}")
 
 
-def test_moving_invalid_tap_is_ignored_and_flagged(rend):
+@pytest.mark.parametrize("L", [2000, 2048])          # the warp-gather and the TMEM kernel
+def test_moving_invalid_tap_is_ignored_and_flagged(rend, L):
     from paper_1502_03162_gb300 import hrir
     rng = np.random.default_rng(12)
-    y, idx, w, nnz, res, mi, mw, mn = _moving_case(rng, 2, 2000, 256, 16)
+    y, idx, w, nnz, res, mi, mw, mn = _moving_case(rng, 2, L, 256, 16)
     rend.load_filters(idx, w, nnz, 200, res)
     bad = mi.copy()
     bad[0, 1, 0, 0] = 250                     # >= Lg
     mw2 = mw.copy()
     mw2[0, 1, 0, 0] = 0.0                     # the reference: that tap silent
-    ref = oracle.render_moving(y, mi, mw2, mn, 256, 200, res, length=2000)
+    ref = oracle.render_moving(y, mi, mw2, mn, 256, 200, res, length=L)
     dev = lambda a, dt=None: torch.from_numpy(np.ascontiguousarray(a).view(dt) if dt else  # noqa: E731
                                               np.ascontiguousarray(a)).cuda()
     out = hrir.hrir_render_moving(rend.ctx, dev(y), dev(bad, np.int16), dev(mw), dev(mn), 256,
-                                  length=2000).cpu().numpy()
+                                  length=L).cpu().numpy()
     assert rend.sync() == hrir.HRIR_EINVAL
     assert rend.sync() == 0
     assert_close(out, ref, what="bad tap ignored")
