@@ -206,68 +206,79 @@ __device__ __forceinline__ void build_progs(const MovingTmemArgs &a, const TileR
                                             const int (&er)[3], const int (&ep)[3], const uint16_t *tidx,
                                             const float *tw, Prog *prog0, Prog *prog1, int lane, int my_nnz)
 {
+    // both ears' programs are built step by step side by side (independent latency chains)
     const int k = a.k_max;
+    if (lane < 8) prog0->bits[lane] = 0u;
+    else if (lane < 16) prog1->bits[lane - 8] = 0u;
+    // this lane's entries (row, offset, weight) per ear; row -1 where there is none
+    int ent_o[2][3], ent_r[2][3];
+    float ent_w[2][3];
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        Prog *pg = e ? prog1 : prog0;
-        if (lane < 8) pg->bits[lane] = 0u;
-        // this lane's entries (row, offset, weight); row -1 where there is none
-        int ent_o[3], ent_r[3];
-        float ent_w[3];
+    for (int e = 0; e < 2; ++e)
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
             const int r = er[m], p = ep[m];
             const int nz = __shfl_sync(0xffffffffu, my_nnz, (r < qr.nrows ? r : 0) * 2 + e);
-            ent_r[m] = -1;
-            ent_o[m] = 0;
-            ent_w[m] = 0.f;
-            if (r < qr.nrows && p < nz) {
-                if (nz > k && p == 0) atomicOr(a.status, DEV_BAD_TAP);
-                const int rs = qr.jlo + r - tr.lo;          // staged row
-                const int o = tidx[(rs * 2 + e) * k + p];
-                if (o < a.refl_len) {
-                    ent_o[m] = o;
-                    ent_w[m] = tw[(rs * 2 + e) * k + p];
-                    ent_r[m] = r;
-                } else {
-                    atomicOr(a.status, DEV_BAD_TAP);
-                }
-            }
+            const bool live = r < qr.nrows && p < nz;
+            const int rs = qr.jlo + r - tr.lo;              // staged row
+            const int o = live ? (int)tidx[(rs * 2 + e) * k + p] : 0;
+            const float wv = live ? tw[(rs * 2 + e) * k + p] : 0.f;
+            if (live && ((nz > k && p == 0) || o >= a.refl_len)) atomicOr(a.status, DEV_BAD_TAP);
+            const bool ok = live && o < a.refl_len;
+            ent_r[e][m] = ok ? r : -1;
+            ent_o[e][m] = ok ? o : 0;
+            ent_w[e][m] = wv;
         }
-        __syncwarp();
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        Prog *pg = e ? prog1 : prog0;
 #pragma unroll
         for (int m = 0; m < 3; ++m)
-            if (ent_r[m] >= 0) atomicOr(&pg->bits[ent_o[m] >> 5], 1u << (ent_o[m] & 31));
-        __syncwarp();
-        // lanes 0 .. kWords - 1: a word of the union and the count of the words below it
-        const uint32_t word = lane < kWords ? pg->bits[lane] : 0u;
-        int incl = __popc(word);
+            if (ent_r[e][m] >= 0) atomicOr(&pg->bits[ent_o[e][m] >> 5], 1u << (ent_o[e][m] & 31));
+    }
+    __syncwarp();
+    // lanes 8 e + w (w < kWords): word w of ear e's union and the count of the words below it
+    // (one scan in segments of 8 lanes for both ears)
+    const int sl = lane & 7;
+    const Prog *pl = lane < 8 ? prog0 : prog1;
+    const uint32_t word = (lane < 16 && sl < kWords) ? pl->bits[sl] : 0u;
+    int incl = __popc(word);
 #pragma unroll
-        for (int d = 1; d < 8; d <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += v;
-        }
-        const int excl = incl - __popc(word);
-        const int n = __shfl_sync(0xffffffffu, incl, kWords - 1);
-        // zero the weight rows of the n entries and of the two padding entries
+    for (int d = 1; d < 8; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, d, 8);
+        if (sl >= d) incl += v;
+    }
+    const int excl = incl - __popc(word);
+    int n[2];
+    n[0] = __shfl_sync(0xffffffffu, incl, kWords - 1);
+    n[1] = __shfl_sync(0xffffffffu, incl, 8 + kWords - 1);
+    // zero the weight rows of the n entries and of the two padding entries
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        Prog *pg = e ? prog1 : prog0;
         float4 *wz = reinterpret_cast<float4 *>(&pg->w[0][0]);
-        for (int i = lane; i < ((n + 2) * kRowsQ + 3) / 4; i += 32) wz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (lane < 2) pg->col[n + lane] = 0;
-        if (lane == 0) pg->n = n;
-        __syncwarp();
-        // entry (row r, offset o) goes to union rank(o) = offsets below o
+        for (int i = lane; i < ((n[e] + 2) * kRowsQ + 3) / 4; i += 32) wz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane < 2) pg->col[n[e] + lane] = 0;
+        if (lane == 0) pg->n = n[e];
+    }
+    __syncwarp();
+    // entry (row r, offset o) goes to union rank(o) = offsets below o
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        Prog *pg = e ? prog1 : prog0;
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-            const int o = ent_o[m], wd = o >> 5;
-            const int u = __shfl_sync(0xffffffffu, excl, wd) +
-                          __popc(__shfl_sync(0xffffffffu, word, wd) & ((1u << (o & 31)) - 1u));
-            if (ent_r[m] >= 0) {
+            const int o = ent_o[e][m], src = 8 * e + (o >> 5);
+            const int u = __shfl_sync(0xffffffffu, excl, src) +
+                          __popc(__shfl_sync(0xffffffffu, word, src) & ((1u << (o & 31)) - 1u));
+            if (ent_r[e][m] >= 0) {
                 pg->col[u] = SW - o;
-                pg->w[u][ent_r[m]] = ent_w[m];
+                pg->w[u][ent_r[e][m]] = ent_w[e][m];
             }
         }
-        __syncwarp();
     }
+    __syncwarp();
 }
 
 // Shared memory: [stages] windows (1024-byte aligned), [stages] table blocks, barriers (full,
