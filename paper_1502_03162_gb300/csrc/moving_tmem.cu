@@ -36,8 +36,9 @@ constexpr int RS = R / 2;           // outputs per tap warp (two halves)
 constexpr int RP = RS / 2;          // packed pairs per accumulator set
 constexpr int NQ = 4;               // TMEM lane quarters
 constexpr int NTW = 16;             // tap warps: (quarter, ear, half)
-constexpr int NC = NTW + NQ;        // compute warps
-constexpr int NW = NC + 1;          // + the producer
+constexpr int NC = NTW + NQ;        // tap and copy warps
+constexpr int NB = NQ;              // program builders, one per lane quarter
+constexpr int NW = NC + NB;         // (the builder of quarter 0 also issues the loads)
 constexpr int kCols = kMvCols;
 constexpr int SW = kMvSpan;         // 224 filter offsets per window
 constexpr int kWords = (SW + 31) / 32;   // union bitmask words
@@ -286,7 +287,7 @@ __device__ __forceinline__ void build_progs(const MovingTmemArgs &a, const TileR
 // empty per stage; full, empty per quarter and window buffer), abort flag, TMEM slot, last
 // issued unit per stage, then the tap programs and the fold accumulators at the offsets the
 // launcher passes.
-// 21 warps put 6 on SM sub-partition 0, whose 16384 registers then allow at most 85 a thread
+// 24 warps put 6 on each SM sub-partition, whose 16384 registers then allow at most 85 a thread
 __global__ void __maxnreg__(80) moving_tmem_kernel(const __grid_constant__ CUtensorMap tmap3, const MovingTmemArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -309,10 +310,10 @@ __global__ void __maxnreg__(80) moving_tmem_kernel(const __grid_constant__ CUten
         prefetch_tensormap(&tmap3);
         for (int i = 0; i < stages; ++i) {
             mbar_init(smem_addr(&bars[i]), 1);              // full: producer + tx bytes
-            mbar_init(smem_addr(&bars[stages + i]), NQ);    // empty: the copy warps
+            mbar_init(smem_addr(&bars[stages + i]), NQ + NB);   // empty: copy warps, builders
         }
         for (int i = 0; i < 2 * NQ; ++i) {
-            mbar_init(smem_addr(&wbars[i]), 1);             // window full: the copy warp
+            mbar_init(smem_addr(&wbars[i]), 2);             // window full: copy warp + builder
             mbar_init(smem_addr(&wbars[2 * NQ + i]), 4);    // window empty: the quarter's tap warps
         }
         *abort_flag = 0;
@@ -337,34 +338,7 @@ __global__ void __maxnreg__(80) moving_tmem_kernel(const __grid_constant__ CUten
     pos0.t = (int)(u_begin / a.n_src);
     pos0.s = (int)(u_begin - (int64_t)pos0.t * a.n_src);
 
-    if (n_units > 0 && warp == NW - 1) {
-        // ---- producer: fills the ring, then refills each stage once the copy warps released it
-        UnitPos p = pos0;
-        for (int k0 = 0; k0 < n_units && k0 < stages; ++k0) {
-            if (lane == 0) {
-                issue_unit(&tmap3, a, p.t, p.s, smem_addr(wins + (size_t)k0 * kWinBytes),
-                           smem_addr(tbls + (size_t)k0 * kStageTableBytes), smem_addr(&bars[k0]));
-                last_issued[k0] = k0;
-            }
-            p.advance(1, a.n_src);
-        }
-        int st = 0;
-        uint32_t ph = 0;
-        for (int r = 0; r + stages < n_units; ++r) {
-            if (!mbar_wait_bounded(smem_addr(&bars[stages + st]), ph, abort_flag, a.status)) break;
-            if (lane == 0) {
-                issue_unit(&tmap3, a, p.t, p.s, smem_addr(wins + (size_t)st * kWinBytes),
-                           smem_addr(tbls + (size_t)st * kStageTableBytes), smem_addr(&bars[st]));
-                last_issued[st] = r + stages;
-            }
-            __syncwarp();
-            p.advance(1, a.n_src);
-            if (++st == stages) {
-                st = 0;
-                ph ^= 1u;
-            }
-        }
-    } else if (n_units > 0) {
+    if (n_units > 0) {
         const int q = warp & (NQ - 1);
         const uint32_t tq = tmem_base + ((uint32_t)(32 * q) << 16);
         const int lrow = q * 32 + lane;                      // TMEM lane = tile row
@@ -373,8 +347,8 @@ __global__ void __maxnreg__(80) moving_tmem_kernel(const __grid_constant__ CUten
         int st = 0;
         uint32_t ph = 0;
         UnitPos pos = pos0;
-        if (warp >= NTW) {
-            // ---- copy warp of lane quarter q: tap programs, then the window into TMEM ----
+        if (warp >= NC) {
+            // ---- builder of lane quarter q: the quarter's tap programs (both ears) ----
             // this lane's entry slots: i = lane + 32 m -> row i / k_max, position i % k_max
             int er[3], ep[3];
 #pragma unroll
@@ -387,6 +361,66 @@ __global__ void __maxnreg__(80) moving_tmem_kernel(const __grid_constant__ CUten
             TileRows tr = tile_rows(a, pos.t);
             QuarterRows qr = quarter_rows(a, pos.t, q);
             int nnz_cur = load_nnz(a, qr, pos.s, lane);
+            // quarter 0's builder also fills the ring, then refills the stage of unit k - 1
+            // (unit k - 1 + stages) at the start of unit k, once the copy warps and builders
+            // released it
+            const bool producer = q == 0;
+            UnitPos p_iss = pos0;
+            int st_r = 0;
+            uint32_t ph_r = 0;
+            if (producer) {
+                for (int k0 = 0; k0 < n_units && k0 < stages; ++k0) {
+                    if (lane == 0) {
+                        issue_unit(&tmap3, a, p_iss.t, p_iss.s, smem_addr(wins + (size_t)k0 * kWinBytes),
+                                   smem_addr(tbls + (size_t)k0 * kStageTableBytes), smem_addr(&bars[k0]));
+                        last_issued[k0] = k0;
+                    }
+                    p_iss.advance(1, a.n_src);
+                }
+            }
+            for (int k = 0; k < n_units; ++k) {
+                const uint32_t buf = (uint32_t)k & 1u;
+                if (producer && k >= 1 && k - 1 + stages < n_units) {
+                    if (!mbar_wait_bounded(smem_addr(&bars[stages + st_r]), ph_r, abort_flag, a.status)) break;
+                    if (lane == 0) {
+                        issue_unit(&tmap3, a, p_iss.t, p_iss.s, smem_addr(wins + (size_t)st_r * kWinBytes),
+                                   smem_addr(tbls + (size_t)st_r * kStageTableBytes), smem_addr(&bars[st_r]));
+                        last_issued[st_r] = k - 1 + stages;
+                    }
+                    __syncwarp();
+                    p_iss.advance(1, a.n_src);
+                    if (++st_r == stages) {
+                        st_r = 0;
+                        ph_r ^= 1u;
+                    }
+                }
+                if (!mbar_wait_bounded(smem_addr(&bars[st]), ph, abort_flag, a.status)) break;
+                if (k >= 2 && !mbar_wait_bounded(win_empty + 8 * buf, (uint32_t)((k >> 1) - 1) & 1u, abort_flag,
+                                                 a.status))
+                    break;
+                const unsigned char *tb = tbls + (size_t)st * kStageTableBytes;
+                build_progs(a, tr, qr, er, ep, reinterpret_cast<const uint16_t *>(tb),
+                            reinterpret_cast<const float *>(tb + kTableIdxBytes),
+                            progs + (buf * NQ + q) * 2, progs + (buf * NQ + q) * 2 + 1, lane, nnz_cur);
+                if (lane == 0) {
+                    mbar_arrive(win_full + 8 * buf);                   // programs ready
+                    mbar_arrive(smem_addr(&bars[stages + st]));        // tables no longer read
+                }
+                UnitPos nx = pos;                             // the next unit's nnz, in flight
+                nx.advance(1, a.n_src);
+                if (k + 1 < n_units && nx.t != pos.t) {
+                    tr = tile_rows(a, nx.t);
+                    qr = quarter_rows(a, nx.t, q);
+                }
+                nnz_cur = k + 1 < n_units ? load_nnz(a, qr, nx.s, lane) : 0;
+                pos = nx;
+                if (++st == stages) {
+                    st = 0;
+                    ph ^= 1u;
+                }
+            }
+        } else if (warp >= NTW) {
+            // ---- copy warp of lane quarter q: the window into TMEM ----
             for (int k = 0; k < n_units; ++k) {
                 const uint32_t buf = (uint32_t)k & 1u;
                 if (!mbar_wait_bounded(smem_addr(&bars[st]), ph, abort_flag, a.status)) break;
@@ -394,19 +428,6 @@ __global__ void __maxnreg__(80) moving_tmem_kernel(const __grid_constant__ CUten
                                                  a.status))
                     break;
                 tc_fence_after();
-                const unsigned char *tb = tbls + (size_t)st * kStageTableBytes;
-                build_progs(a, tr, qr, er, ep, reinterpret_cast<const uint16_t *>(tb),
-                            reinterpret_cast<const float *>(tb + kTableIdxBytes),
-                            progs + (buf * NQ + q) * 2, progs + (buf * NQ + q) * 2 + 1, lane, nnz_cur);
-                {
-                    UnitPos nx = pos;                         // the next unit's nnz, in flight
-                    nx.advance(1, a.n_src);
-                    if (k + 1 < n_units && nx.t != pos.t) {
-                        tr = tile_rows(a, nx.t);
-                        qr = quarter_rows(a, nx.t, q);
-                    }
-                    nnz_cur = k + 1 < n_units ? load_nnz(a, qr, nx.s, lane) : 0;
-                }
                 // window of TMEM lane lrow: tile rows rr0 .. rr0 + 7 (32 samples each),
                 // rr0 = (halo + 32 lrow - SW) / 32; row r's 16-byte chunk c at c ^ (r % 8)
                 const unsigned char *wb = wins + (size_t)st * kWinBytes;
@@ -429,10 +450,9 @@ __global__ void __maxnreg__(80) moving_tmem_kernel(const __grid_constant__ CUten
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(win_full + 8 * buf);                   // programs and window ready
+                    mbar_arrive(win_full + 8 * buf);                   // window ready
                     mbar_arrive(smem_addr(&bars[stages + st]));        // the stage is no longer read
                 }
-                pos.advance(1, a.n_src);
                 if (++st == stages) {
                     st = 0;
                     ph ^= 1u;
