@@ -29,10 +29,13 @@ __device__ __forceinline__ void topk_load(const float *__restrict__ g, int row, 
     }
 }
 
+// hint: a threshold that separated the k largest keys of an earlier, similar row (0: none);
+// it only shortens the search (the selected set does not depend on it).  Returns the
+// threshold found for this row (or hint when every positive entry is taken).
 template <int MAXPER>
-__device__ __forceinline__ void topk_row(const float (&v)[MAXPER], int row, int j0, int lane, int k,
-                                         uint16_t *__restrict__ idx, float *__restrict__ w,
-                                         uint8_t *__restrict__ nnz)
+__device__ __forceinline__ uint32_t topk_row(const float (&v)[MAXPER], int row, int j0, int lane, int k,
+                                             uint32_t hint, uint16_t *__restrict__ idx, float *__restrict__ w,
+                                             uint8_t *__restrict__ nnz)
 {
     // Keys: the bits of a strictly positive float order like the float; 0 = not selectable.
     // The selected set is every key above T plus the first ties at T in index order, where T
@@ -64,7 +67,19 @@ __device__ __forceinline__ void topk_row(const float (&v)[MAXPER], int row, int 
         cnt = total;
     } else {
         uint32_t lo = 1, hi = __reduce_max_sync(0xffffffffu, kmax) + 1u;   // #(>= lo) >= k > #(>= hi)
-        if (k <= 32) {
+        bool exact = false;
+        if (hint > 1u && hint < hi) {
+            // one count at the earlier row's threshold: exact for a row whose k-th and
+            // (k + 1)-th keys still straddle it, else a bound for the search below
+            const int c = count_ge(hint);
+            if (c >= k) {
+                lo = hint;
+                exact = c == k;
+            } else {
+                hi = hint;
+            }
+        }
+        if (!exact && k <= 32) {
             // a tighter start: the k-th largest lane maximum (k lanes hold a key at least that
             // large), from a bitonic sort of the 32 lane maxima (ascending across the lanes)
             uint32_t x = kmax;
@@ -78,10 +93,9 @@ __device__ __forceinline__ void topk_row(const float (&v)[MAXPER], int row, int 
                 }
             }
             const uint32_t kth = __shfl_sync(0xffffffffu, x, 32 - k);
-            lo = kth > 1u ? kth : 1u;
+            lo = kth > lo ? kth : lo;
         }
-        bool exact = false;
-        while (hi - lo > 1u) {
+        while (!exact && hi - lo > 1u) {
             const uint32_t mid = lo + (hi - lo) / 2u;
             const int c = count_ge(mid);
             if (c >= k) {
@@ -122,6 +136,7 @@ __device__ __forceinline__ void topk_row(const float (&v)[MAXPER], int row, int 
             }
         }
         cnt = k;
+        hint = lo;                              // a threshold inside this row's gap
     }
     // ascending-index output: lanes hold ascending slices; prefix-count the kept entries
     const int mine = MAXPER <= 32 ? __popc((uint32_t)taken) : __popcll((uint64_t)taken);
@@ -148,6 +163,7 @@ __device__ __forceinline__ void topk_row(const float (&v)[MAXPER], int row, int 
         rw[t] = 0.f;
     }
     if (lane == 0) nnz[row] = (uint8_t)cnt;
+    return hint;
 }
 
 template <int MAXPER>
@@ -155,16 +171,24 @@ __global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, 
                                                    int refl_len, int k, uint16_t *__restrict__ idx,
                                                    float *__restrict__ w, uint8_t *__restrict__ nnz)
 {
+    // each warp takes a contiguous run of rows, so that row r - 2 (the same ear of the
+    // previous segment or direction in the (.., ear) row order) gives row r's search a start
     const int lane = threadIdx.x & 31;
-    const int n_warps = gridDim.x * 4;
+    const int64_t n_warps = (int64_t)gridDim.x * 4;
+    const int64_t chunk = ((int64_t)n_rows + n_warps - 1) / n_warps;
+    const int64_t wid = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int r0 = (int)(wid * chunk < n_rows ? wid * chunk : n_rows);
+    const int r1 = (int)(r0 + chunk < n_rows ? r0 + chunk : n_rows);
     const int per = (refl_len + 31) / 32;
     const int j0 = lane * per;
-    int row = blockIdx.x * 4 + (threadIdx.x >> 5);
     float v[MAXPER], vn[MAXPER];
-    topk_load<MAXPER>(g, row, n_rows, refl_len, per, j0, v);
-    for (; row < n_rows; row += n_warps) {
-        topk_load<MAXPER>(g, row + n_warps, n_rows, refl_len, per, j0, vn);   // in flight
-        topk_row<MAXPER>(v, row, j0, lane, k, idx, w, nnz);
+    uint32_t hint0 = 0u, hint1 = 0u;             // the last thresholds of even and odd rows
+    topk_load<MAXPER>(g, r0 < r1 ? r0 : n_rows, n_rows, refl_len, per, j0, v);
+    for (int row = r0; row < r1; ++row) {
+        topk_load<MAXPER>(g, row + 1 < r1 ? row + 1 : n_rows, n_rows, refl_len, per, j0, vn);   // in flight
+        const uint32_t h = topk_row<MAXPER>(v, row, j0, lane, k, (row & 1) ? hint1 : hint0, idx, w, nnz);
+        if (row & 1) hint1 = h;
+        else hint0 = h;
 #pragma unroll
         for (int j = 0; j < MAXPER; ++j) v[j] = vn[j];
     }
