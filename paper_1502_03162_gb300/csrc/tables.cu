@@ -181,16 +181,23 @@ __global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, 
     const int r1 = (int)(r0 + chunk < n_rows ? r0 + chunk : n_rows);
     const int per = (refl_len + 31) / 32;
     const int j0 = lane * per;
-    float v[MAXPER], vn[MAXPER];
-    uint32_t hint0 = 0u, hint1 = 0u;             // the last thresholds of even and odd rows
-    topk_load<MAXPER>(g, r0 < r1 ? r0 : n_rows, n_rows, refl_len, per, j0, v);
-    for (int row = r0; row < r1; ++row) {
-        topk_load<MAXPER>(g, row + 1 < r1 ? row + 1 : n_rows, n_rows, refl_len, per, j0, vn);   // in flight
-        const uint32_t h = topk_row<MAXPER>(v, row, j0, lane, k, (row & 1) ? hint1 : hint0, idx, w, nnz);
-        if (row & 1) hint1 = h;
-        else hint0 = h;
+    // D rows in flight per warp (the loads of rows row + D .. are issued as each buffer frees)
+    constexpr int D = MAXPER <= 16 ? 3 : 1;
+    float v[D][MAXPER];
 #pragma unroll
-        for (int j = 0; j < MAXPER; ++j) v[j] = vn[j];
+    for (int d = 0; d < D; ++d) topk_load<MAXPER>(g, r0 + d < r1 ? r0 + d : n_rows, n_rows, refl_len, per, j0, v[d]);
+    uint32_t hint0 = 0u, hint1 = 0u;             // the last thresholds of even and odd rows
+    for (int row = r0; row < r1; row += D) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int r = row + d;
+            if (r < r1) {
+                const uint32_t h = topk_row<MAXPER>(v[d], r, j0, lane, k, (r & 1) ? hint1 : hint0, idx, w, nnz);
+                if (r & 1) hint1 = h;
+                else hint0 = h;
+            }
+            topk_load<MAXPER>(g, r + D < r1 ? r + D : n_rows, n_rows, refl_len, per, j0, v[d]);
+        }
     }
 }
 
