@@ -298,6 +298,11 @@ int hrir_mlp_adam(hrir_ctx *ctx, int64_t n, float *params, const float *grads, f
  *             An index >= Lg or a count > k_max is ignored and flags HRIR_EINVAL for
  *             hrir_sync.
  *   seg_len   a multiple of 128;  1 <= k_max <= 255.
+ * With seg_len >= 256, len % 32 == 0, k_max % 4 == 0, k_max <= 16, Lg <= 224 and 16-byte
+ * aligned tables the mix runs on tensor-memory windows (per lane quarter, the union of the
+ * tap offsets of the segments it spans is applied with each row's weight, 0 where a row lacks
+ * an offset); otherwise it gathers the source samples from shared memory.  Both give the
+ * same sums up to FP32 rounding order.
  * ------------------------------------------------------------------------------------- */
 int hrir_render_moving(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, const float *src,
                        int n_seg, int seg_len, int k_max, const uint16_t *tap_idx,
