@@ -29,6 +29,21 @@ __device__ __forceinline__ void topk_load(const float *__restrict__ g, int row, 
     }
 }
 
+// Rows of a multiple of 8 values at 16-byte aligned addresses: lane l takes the 8 values
+// [8 l, 8 l + 8) by two 16-byte loads (lanes past the row take zeros).
+__device__ __forceinline__ void topk_load_vec8(const float *__restrict__ g, int row, int n_rows, int refl_len, int j0,
+                                               float (&v)[8])
+{
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    if (row < n_rows && j0 < refl_len) {
+        const float4 *gr = reinterpret_cast<const float4 *>(g + (size_t)row * refl_len + j0);
+        a = __ldg(gr);
+        b = __ldg(gr + 1);
+    }
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
 // hint: a threshold that separated the k largest keys of an earlier, similar row (0: none);
 // it only shortens the search (the selected set does not depend on it).  Returns the
 // threshold found for this row (or hint when every positive entry is taken).
@@ -166,7 +181,7 @@ __device__ __forceinline__ uint32_t topk_row(const float (&v)[MAXPER], int row, 
     return hint;
 }
 
-template <int MAXPER>
+template <int MAXPER, bool VEC8>
 __global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, int n_rows,
                                                    int refl_len, int k, uint16_t *__restrict__ idx,
                                                    float *__restrict__ w, uint8_t *__restrict__ nnz)
@@ -179,13 +194,17 @@ __global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, 
     const int64_t wid = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
     const int r0 = (int)(wid * chunk < n_rows ? wid * chunk : n_rows);
     const int r1 = (int)(r0 + chunk < n_rows ? r0 + chunk : n_rows);
-    const int per = (refl_len + 31) / 32;
+    const int per = VEC8 ? 8 : (refl_len + 31) / 32;
     const int j0 = lane * per;
+    auto load = [&](int r, float (&v)[MAXPER]) {
+        if constexpr (VEC8) topk_load_vec8(g, r, n_rows, refl_len, j0, v);
+        else topk_load<MAXPER>(g, r, n_rows, refl_len, per, j0, v);
+    };
     // D rows in flight per warp (the loads of rows row + D .. are issued as each buffer frees)
     constexpr int D = MAXPER <= 16 ? 3 : 1;
     float v[D][MAXPER];
 #pragma unroll
-    for (int d = 0; d < D; ++d) topk_load<MAXPER>(g, r0 + d < r1 ? r0 + d : n_rows, n_rows, refl_len, per, j0, v[d]);
+    for (int d = 0; d < D; ++d) load(r0 + d < r1 ? r0 + d : n_rows, v[d]);
     uint32_t hint0 = 0u, hint1 = 0u;             // the last thresholds of even and odd rows
     for (int row = r0; row < r1; row += D) {
 #pragma unroll
@@ -196,7 +215,7 @@ __global__ void __launch_bounds__(128) topk_kernel(const float *__restrict__ g, 
                 if (r & 1) hint1 = h;
                 else hint0 = h;
             }
-            topk_load<MAXPER>(g, r + D < r1 ? r + D : n_rows, n_rows, refl_len, per, j0, v[d]);
+            load(r + D < r1 ? r + D : n_rows, v[d]);
         }
     }
 }
@@ -297,10 +316,12 @@ cudaError_t launch_topk(const float *g, int n_rows, int refl_len, int k, uint16_
         const int64_t need = ((int64_t)n_rows + 3) / 4, wave = (int64_t)sms * per_sm;
         kern<<<(unsigned)(need < wave ? need : wave), 128, 0, st>>>(g, n_rows, refl_len, k, idx, w, nnz);
     };
-    if (per <= 8) launch(topk_kernel<8>);
-    else if (per <= 16) launch(topk_kernel<16>);
-    else if (per <= 32) launch(topk_kernel<32>);
-    else launch(topk_kernel<64>);
+    if (refl_len % 8 == 0 && refl_len <= 256 && (reinterpret_cast<uintptr_t>(g) & 15) == 0)
+        launch(topk_kernel<8, true>);          // 8 values a lane, two 16-byte loads
+    else if (per <= 8) launch(topk_kernel<8, false>);
+    else if (per <= 16) launch(topk_kernel<16, false>);
+    else if (per <= 32) launch(topk_kernel<32, false>);
+    else launch(topk_kernel<64, false>);
     return cudaGetLastError();
 }
 
