@@ -39,7 +39,8 @@ def _params(rng, refl_len):
     return p
 
 
-@pytest.mark.parametrize("B,refl_len", [(300, 200), (77, 33), (1, 200)])
+# 2500 rows: the training step's size, whose backward products are split over K
+@pytest.mark.parametrize("B,refl_len", [(300, 200), (77, 33), (1, 200), (2500, 200)])
 def test_mlp_forward_backward_match_oracle(rend, B, refl_len):
     from paper_1502_03162_gb300 import hrir
     rng = np.random.default_rng(B + refl_len)
