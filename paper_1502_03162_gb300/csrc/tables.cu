@@ -58,100 +58,104 @@ __device__ __forceinline__ uint32_t topk_row(const float (&v)[MAXPER], int row, 
     // the key bits (warp-wide counts), stopping early when exactly k keys are >= t.
     using Mask = typename std::conditional<(MAXPER <= 32), uint32_t, uint64_t>::type;
     uint32_t key[MAXPER];
-    int n_pos = 0;
-    uint32_t kmax = 0;
 #pragma unroll
-    for (int j = 0; j < MAXPER; ++j) {
-        key[j] = v[j] > 0.f ? __float_as_uint(v[j]) : 0u;
-        n_pos += key[j] != 0u;
-        kmax = key[j] > kmax ? key[j] : kmax;
-    }
+    for (int j = 0; j < MAXPER; ++j) key[j] = v[j] > 0.f ? __float_as_uint(v[j]) : 0u;
     auto count_ge = [&](uint32_t t) {
         int c = 0;
 #pragma unroll
         for (int j = 0; j < MAXPER; ++j) c += key[j] >= t;
         return (int)__reduce_add_sync(0xffffffffu, (uint32_t)c);
     };
-    const int total = (int)__reduce_add_sync(0xffffffffu, (uint32_t)n_pos);
+    // first one count at the earlier row's threshold: when exactly k keys lie at or above it
+    // (a row whose k-th and (k + 1)-th keys still straddle it) those are the selection
+    const int c_hint = hint > 1u ? count_ge(hint) : -1;
     Mask taken = 0;
     int cnt;
-    if (total <= k) {                       // every positive entry
+    if (c_hint == k) {
 #pragma unroll
         for (int j = 0; j < MAXPER; ++j)
-            if (key[j]) taken |= (Mask)1 << j;
-        cnt = total;
+            if (key[j] >= hint) taken |= (Mask)1 << j;
+        cnt = k;
     } else {
-        uint32_t lo = 1, hi = __reduce_max_sync(0xffffffffu, kmax) + 1u;   // #(>= lo) >= k > #(>= hi)
-        bool exact = false;
-        if (hint > 1u && hint < hi) {
-            // one count at the earlier row's threshold: exact for a row whose k-th and
-            // (k + 1)-th keys still straddle it, else a bound for the search below
-            const int c = count_ge(hint);
-            if (c >= k) {
-                lo = hint;
-                exact = c == k;
-            } else {
-                hi = hint;
-            }
-        }
-        if (!exact && k <= 32) {
-            // a tighter start: the k-th largest lane maximum (k lanes hold a key at least that
-            // large), from a bitonic sort of the 32 lane maxima (ascending across the lanes)
-            uint32_t x = kmax;
+        int n_pos = 0;
+        uint32_t kmax = 0;
 #pragma unroll
-            for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, stride);
-                    const bool asc = (lane & size) == 0, lower = (lane & stride) == 0;
-                    x = (asc == lower) ? (x < y ? x : y) : (x > y ? x : y);
-                }
-            }
-            const uint32_t kth = __shfl_sync(0xffffffffu, x, 32 - k);
-            lo = kth > lo ? kth : lo;
+        for (int j = 0; j < MAXPER; ++j) {
+            n_pos += key[j] != 0u;
+            kmax = key[j] > kmax ? key[j] : kmax;
         }
-        while (!exact && hi - lo > 1u) {
-            const uint32_t mid = lo + (hi - lo) / 2u;
-            const int c = count_ge(mid);
-            if (c >= k) {
-                lo = mid;
-                if (c == k) {
-                    exact = true;
-                    break;
-                }
-            } else {
-                hi = mid;
-            }
-        }
-        if (exact) {
+        const int total = (int)__reduce_add_sync(0xffffffffu, (uint32_t)n_pos);
+        if (total <= k) {                       // every positive entry
 #pragma unroll
             for (int j = 0; j < MAXPER; ++j)
-                if (key[j] >= lo) taken |= (Mask)1 << j;
+                if (key[j]) taken |= (Mask)1 << j;
+            cnt = total;
         } else {
-            // lo is the k-th largest key: every key above it, then its ties in index order
-            int need = k - count_ge(lo + 1u);
-            int ties = 0;
-#pragma unroll
-            for (int j = 0; j < MAXPER; ++j) ties += key[j] == lo;
-            int before_t = ties;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int o = __shfl_up_sync(0xffffffffu, before_t, off);
-                if (lane >= off) before_t += o;
+            uint32_t lo = 1, hi = __reduce_max_sync(0xffffffffu, kmax) + 1u;   // #(>= lo) >= k > #(>= hi)
+            bool exact = false;
+            if (c_hint >= 0 && hint < hi) {     // the earlier row's threshold as a bound
+                if (c_hint > k) lo = hint;
+                else hi = hint;
             }
-            need -= before_t - ties;        // ties already taken by lower lanes
+            if (!exact && k <= 32) {
+                // a tighter start: the k-th largest lane maximum (k lanes hold a key at least that
+                // large), from a bitonic sort of the 32 lane maxima (ascending across the lanes)
+                uint32_t x = kmax;
 #pragma unroll
-            for (int j = 0; j < MAXPER; ++j) {
-                if (key[j] > lo) {
-                    taken |= (Mask)1 << j;
-                } else if (key[j] == lo && need > 0) {
-                    taken |= (Mask)1 << j;
-                    --need;
+                for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, stride);
+                        const bool asc = (lane & size) == 0, lower = (lane & stride) == 0;
+                        x = (asc == lower) ? (x < y ? x : y) : (x > y ? x : y);
+                    }
+                }
+                const uint32_t kth = __shfl_sync(0xffffffffu, x, 32 - k);
+                lo = kth > lo ? kth : lo;
+            }
+            while (!exact && hi - lo > 1u) {
+                const uint32_t mid = lo + (hi - lo) / 2u;
+                const int c = count_ge(mid);
+                if (c >= k) {
+                    lo = mid;
+                    if (c == k) {
+                        exact = true;
+                        break;
+                    }
+                } else {
+                    hi = mid;
                 }
             }
+            if (exact) {
+#pragma unroll
+                for (int j = 0; j < MAXPER; ++j)
+                    if (key[j] >= lo) taken |= (Mask)1 << j;
+            } else {
+                // lo is the k-th largest key: every key above it, then its ties in index order
+                int need = k - count_ge(lo + 1u);
+                int ties = 0;
+#pragma unroll
+                for (int j = 0; j < MAXPER; ++j) ties += key[j] == lo;
+                int before_t = ties;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int o = __shfl_up_sync(0xffffffffu, before_t, off);
+                    if (lane >= off) before_t += o;
+                }
+                need -= before_t - ties;        // ties already taken by lower lanes
+#pragma unroll
+                for (int j = 0; j < MAXPER; ++j) {
+                    if (key[j] > lo) {
+                        taken |= (Mask)1 << j;
+                    } else if (key[j] == lo && need > 0) {
+                        taken |= (Mask)1 << j;
+                        --need;
+                    }
+                }
+            }
+            cnt = k;
+            hint = lo;                              // a threshold inside this row's gap
         }
-        cnt = k;
-        hint = lo;                              // a threshold inside this row's gap
     }
     // ascending-index output: lanes hold ascending slices; prefix-count the kept entries
     const int mine = MAXPER <= 32 ? __popc((uint32_t)taken) : __popcll((uint64_t)taken);
