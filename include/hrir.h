@@ -163,7 +163,8 @@ int hrir_render_batch(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld, hri
  * soon as it has landed, while the next ones copy, and the chunk mixes are summed in chunk
  * order.  The result equals hrir_render_batch's up to the order of the FP32 sums (and is
  * deterministic); the call returns when `out` holds it.  Device staging space comes from the
- * context workspace. */
+ * context workspace; `dir` is first copied into a page-locked buffer the context keeps (grown
+ * when a call has more sources than any before it). */
 int hrir_render_batch_host(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld,
                            hrir_dtype dt, const void *src, const int32_t *dir, hrir_mode mode,
                            int full, float *out, int64_t out_ld, void *stream);

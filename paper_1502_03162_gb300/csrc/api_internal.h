@@ -41,6 +41,8 @@ struct hrir_ctx {
     void *d_stage = nullptr;            // device staging for hrir_render_batch_host
     size_t stage_bytes = 0;
     cudaStream_t copy_stream = nullptr; // host-to-device copies of hrir_render_batch_host
+    void *h_dir = nullptr;              // page-locked copy of its direction ids
+    size_t h_dir_bytes = 0;
     cudaEvent_t copy_ev[5] = {};        // [chunks]: chunk copied; [chunks]: caller's work before
     void *d_mlp_ws = nullptr;           // learned-filter network workspace
     size_t mlp_ws_bytes = 0;

@@ -407,6 +407,7 @@ void hrir_destroy(hrir_ctx *ctx)
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     cudaFree(ctx->d_partial);
     cudaFree(ctx->d_stage);
+    if (ctx->h_dir) cudaFreeHost(ctx->h_dir);
     cudaFree(ctx->d_mlp_ws);
     cudaFree(ctx->d_fact_ws);
     cudaFree(ctx->d_view_ws);
@@ -749,6 +750,25 @@ int hrir_render_batch_host(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld
             for (cudaEvent_t &e : ctx->copy_ev) CUDA_TRY(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         }
         cudaStream_t cs = ctx->copy_stream;
+        // the direction ids go through a page-locked copy: a copy from pageable memory would
+        // wait, inside each chunk's issue, for the chunk copies queued before it.  The copy
+        // stream is idle here (every earlier call ended with its synchronize) unless an earlier
+        // call failed half-way; the synchronize makes reusing the page-locked copy safe then too.
+        CUDA_TRY(ctx, cudaStreamSynchronize(cs));
+        const size_t dir_bytes = (size_t)n_src * 4;
+        if (ctx->h_dir_bytes < dir_bytes) {
+            if (ctx->h_dir) cudaFreeHost(ctx->h_dir);
+            ctx->h_dir = nullptr;
+            ctx->h_dir_bytes = 0;
+            if (cudaHostAlloc(&ctx->h_dir, dir_bytes, cudaHostAllocDefault) != cudaSuccess) {
+                cudaGetLastError();
+                ctx->h_dir = nullptr;
+                return fail(ctx, HRIR_ENOMEM, "page-locked staging of %zu bytes failed", dir_bytes);
+            }
+            ctx->h_dir_bytes = dir_bytes;
+        }
+        std::memcpy(ctx->h_dir, dir, dir_bytes);
+        const int32_t *h_dir = static_cast<const int32_t *>(ctx->h_dir);
         // the staging buffers are free once the caller's earlier work on `stream` is done
         CUDA_TRY(ctx, cudaEventRecord(ctx->copy_ev[kHostChunks], st));
         CUDA_TRY(ctx, cudaStreamWaitEvent(cs, ctx->copy_ev[kHostChunks], 0));
@@ -762,7 +782,7 @@ int hrir_render_batch_host(hrir_ctx *ctx, int n_src, int64_t len, int64_t src_ld
                 CUDA_TRY(ctx, cudaMemcpy2DAsync(d_src, dld * es, h_src, src_ld * es, len * es, (size_t)(s1 - s0),
                                                 cudaMemcpyHostToDevice, cs));
             }
-            CUDA_TRY(ctx, cudaMemcpyAsync(d_dir + s0, dir + s0, (size_t)(s1 - s0) * 4, cudaMemcpyHostToDevice, cs));
+            CUDA_TRY(ctx, cudaMemcpyAsync(d_dir + s0, h_dir + s0, (size_t)(s1 - s0) * 4, cudaMemcpyHostToDevice, cs));
             CUDA_TRY(ctx, cudaEventRecord(ctx->copy_ev[c], cs));
         }
         for (int c = 0; c < n_chunks; ++c) {
