@@ -48,15 +48,16 @@ static_assert(RS == 16 && kCols == 256, "x16 slices of 256-column windows");
 constexpr int kRowsQ = kMvSegQ + 1;      // table rows one lane quarter uses
 // tap program of one (lane quarter, ear): n entries of window column and, per table row the
 // quarter uses (rows jlo .. jlo + 4), the row's weight at that offset (0 where it lacks it)
-struct Prog {
+struct alignas(16) Prog {
     int n, pad[3];
     uint32_t bits[8];                   // union of the offsets, one bit per offset
     float w[kProgCap][kRowsQ];
     float w_pad[4];                     // slack for the 16-byte zeroing stores
     int col[kProgCap];
 };
-static_assert(offsetof(Prog, w) % 16 == 0, "16-byte aligned weight rows");
-constexpr int kProgBytes = (int)((sizeof(Prog) + 15) / 16 * 16);
+static_assert(offsetof(Prog, w) % 16 == 0 && sizeof(Prog) % 16 == 0,
+              "16-byte aligned weight rows in every program of an array");
+constexpr int kProgBytes = (int)sizeof(Prog);   // the programs are indexed as an array
 constexpr int kProgsBytes = 2 * NQ * 2 * kProgBytes;   // [window buffer][quarter][ear]
 constexpr int kRunAccBytes = NTW * 2 * RP * 32 * 8;    // fold accumulators, two sets per tap warp
 constexpr int kTableIdxBytes = kMvMaxTableSegs * 2 * kMvMaxK * 2;
