@@ -13,18 +13,19 @@
 // A 4096-output tile is 128 TMEM lanes x 32 outputs; with seg_len % 32 == 0 a lane's outputs
 // lie in one segment, so its weights are one (previous, current) pair per tap.  Each lane's
 // window of 256 samples (224 filter offsets + its 32 outputs) is double-buffered in the 512
-// TMEM columns.  Per (unit = tile x source, lane quarter, ear) the quarter's copy warp builds a
-// tap program in shared memory: the union of the tap offsets of the <= 5 table rows the
+// TMEM columns.  Per (unit = tile x source, lane quarter, ear) the quarter's builder warp makes
+// a tap program in shared memory: the union of the tap offsets of the <= 5 table rows the
 // quarter's segments use (shared-memory bitmask, ranks by a segmented warp scan; both ears'
 // programs side by side), and for each union offset its window column and each row's weight
-// (0 where a row lacks the offset).  The quarter's four tap warps (ear x half) walk the
-// program: a warp-uniform tcgen05.ld of 16 columns (the next entry's load in flight while
-// this one's FMAs run, two register sets), then 8 packed FMAs into the previous and 8 into
-// the current accumulators with the weights of the lane's previous and current rows.  The source tile arrives by one 3-D TMA
+// (0 where a row lacks the offset).  The quarter's copy warp moves the window from the stage
+// into TMEM, and its four tap warps (ear x half) walk the program: a warp-uniform tcgen05.ld
+// of 16 columns (the next entry's load in flight while this one's FMAs run, two register
+// sets), then 8 packed FMAs into the previous and 8 into the current accumulators with the
+// weights of the lane's previous and current rows.  The source tile arrives by one 3-D TMA
 // load of 32-sample rows with the 128-byte swizzle (16-byte chunk c of row r at chunk
 // c ^ (r % 8)), so the copy warps' per-lane row reads hit distinct banks; the table rows of
-// the tile's segments arrive by two bulk copies.  Accumulation over sources, folds, partial
-// slots and bounded waits are those of the static kernel.
+// the tile's segments arrive by two bulk copies, issued by quarter 0's builder.  Accumulation
+// over sources, folds, partial slots and bounded waits are those of the static kernel.
 #include "kernels.h"
 
 namespace hrir {
