@@ -205,7 +205,7 @@ __device__ __forceinline__ int load_nnz(const MovingTmemArgs &a, const QuarterRo
 }
 
 // Build the tap programs of lane quarter q for unit (t, s) from the staged table rows (the
-// quarter's copy warp; every lane calls it).  my_nnz: from load_nnz for this unit.
+// quarter's builder warp; every lane calls it).  my_nnz: from load_nnz for this unit.
 __device__ __forceinline__ void build_progs(const MovingTmemArgs &a, const TileRows &tr, const QuarterRows &qr,
                                             const int (&er)[3], const int (&ep)[3], const uint16_t *tidx,
                                             const float *tw, Prog *prog0, Prog *prog1, int lane, int my_nnz)
