@@ -75,6 +75,33 @@ def test_topk_pack_unaligned_rows_bit_exact(rend, refl_len):
         _check_topk(rend, g, G, k)
 
 
+@pytest.mark.parametrize("refl_len", [200, 203])         # 16-byte row loads / scalar loads
+def test_topk_pack_neighbour_rows_bit_exact(rend, refl_len):
+    """Rows like the network's: row r close to row r - 2 (the same ear of the previous
+    segment), whose threshold the kernel counts first.  Exact copies, tiny drifts that keep or
+    swap the K-th and (K + 1)-th entries, ties planted at the K-th value, all-zero rows and
+    fresh rows, over runs long enough that every warp walks many rows."""
+    rng = np.random.default_rng(refl_len)
+    n_rows = 40000
+    G = np.empty((n_rows, refl_len), np.float32)
+    G[:2] = rng.random((2, refl_len), dtype=np.float32)
+    for r in range(2, n_rows):
+        kind = r % 97
+        if kind == 0 or not G[r - 2].any():
+            G[r] = rng.random(refl_len, dtype=np.float32)                     # fresh row
+        elif kind == 13:
+            G[r] = 0.0                                                        # nothing selectable
+        elif kind % 5 == 0:
+            G[r] = G[r - 2]                                                   # exact copy
+        else:
+            G[r] = G[r - 2] * (1 + 1e-5 * rng.standard_normal(refl_len)).astype(np.float32)
+        if kind % 7 == 3:                                                     # a tie at the 16th value
+            order = np.argsort(-G[r], kind="stable")
+            G[r, order[17]] = G[r, order[15]]
+    for k in (1, 8, 16, 32):
+        _check_topk(rend, _dev(G), G, k)
+
+
 @pytest.mark.parametrize("n_rows,refl_len,k", [(40000, 200, 16), (40001, 128, 32), (20000, 1000, 16)])
 def test_topk_pack_many_rows_bit_exact(rend, n_rows, refl_len, k):
     """More rows than one resident wave of warps: every warp walks several rows."""
