@@ -105,6 +105,10 @@ int hrir_selftest_wait_timeout(hrir_ctx *ctx, void *stream);
  *   w     device, float  [n_rows][k]    out
  *   nnz   device, uint8  [n_rows]       out (number of kept taps, <= k)
  *   0 <= k <= 255.  Bit-exact: indices and weights are copies of input entries.
+ * Speed (not the result) depends on the rows' order: each warp walks a contiguous run of rows
+ * and starts a row's search from the threshold it found two rows before, which is what the
+ * (..., ear) row order of the learned filters offers; refl_len % 8 == 0 (<= 256) with a
+ * 16-byte aligned g takes the faster 16-byte loads.
  * ------------------------------------------------------------------------------------- */
 int hrir_topk_pack(hrir_ctx *ctx, int n_rows, int refl_len, int k, const float *g,
                    uint16_t *idx, float *w, uint8_t *nnz, void *stream);
